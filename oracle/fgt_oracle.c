@@ -1,0 +1,298 @@
+/*
+ * CPU oracle for the 1D Gauss transform and its SOE fast algorithm.
+ *
+ * TEST INFRASTRUCTURE ONLY: plain, slow, FP64, single-threaded unless an
+ * OpenMP thread count is passed.  It shares no code with the CUDA library and
+ * includes none of its headers.  Compile with -ffp-contract=off so that every
+ * product is rounded on its own (no FMA contraction).
+ *
+ *   o1_direct      eqs. 1.1-1.2: u_i = sum_j alpha_j exp(-(x_i - y_j)^2 / (4 delta)),
+ *                  Neumaier-compensated sum over j.
+ *   o2_soe_direct  eqs. 1.3 and 4.1-4.2: u_i = sum_j alpha_j Re sum_k W_k
+ *                  exp(-tau_k |x_i - y_j| / sqrt(delta)) over the halved node set.
+ *   o3_recurrence  Sec. 4: stable sort of the merged points (sources first on
+ *                  equal coordinates, eq. 4.4 puts y_j = x_i in h^+), forward
+ *                  recurrence eq. 4.5 and backward recurrence eq. 4.6 with the
+ *                  exponentials of consecutive gaps, evaluation eq. 4.1 and
+ *                  unpermutation.
+ *   o1_grad / o2_grad  direct O(MN) gradients of L = sum_i g_i u_i with respect to
+ *                  alpha, x, y and delta, for the Gaussian and for the SOE kernel.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_MAX_TERMS 16
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int oracle_openmp_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Neumaier's compensated addition: adds t to (*sum, *comp). */
+static inline void neumaier_add(double* sum, double* comp, double t) {
+    double s2 = *sum + t;
+    if (fabs(*sum) >= fabs(t)) *comp += (*sum - s2) + t;
+    else *comp += (t - s2) + *sum;
+    *sum = s2;
+}
+
+/* O1: direct Gauss transform, eqs. 1.1-1.2. */
+void o1_direct(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+               double delta, double* u, int nthreads) {
+    set_threads(nthreads);
+    const double four_delta = 4.0 * delta;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) if (nthreads != 1)
+#endif
+    for (int64_t i = 0; i < M; ++i) {
+        double sum = 0.0, comp = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double d = x[i] - y[j];
+            neumaier_add(&sum, &comp, alpha[j] * exp(-(d * d) / four_delta));
+        }
+        u[i] = sum + comp;
+    }
+}
+
+/* Real part of W e^{-tau r} for r >= 0: Re(W) e^{-a r} cos(b r) + Im(W) e^{-a r} sin(b r),
+ * with tau = a + i b. */
+static inline double soe_term(double tre, double tim, double wre, double wim, double r) {
+    double mag = exp(-tre * r);
+    return mag * (wre * cos(tim * r) + wim * sin(tim * r));
+}
+
+/* S_n(d; delta) = Re sum_k W_k exp(-tau_k |d| / sqrt(delta)), eq. 1.3 (halved set). */
+static double soe_kernel(int n_e, const double* tre, const double* tim, const double* wre,
+                         const double* wim, double d, double sqrt_delta) {
+    double r = fabs(d) / sqrt_delta;
+    double s = 0.0;
+    for (int k = 0; k < n_e; ++k) s += soe_term(tre[k], tim[k], wre[k], wim[k], r);
+    return s;
+}
+
+/* O2: direct SOE sum, eqs. 1.3, 4.1-4.2. */
+void o2_soe_direct(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                   double delta, int n_e, const double* tre, const double* tim, const double* wre,
+                   const double* wim, double* u, int nthreads) {
+    set_threads(nthreads);
+    const double sd = sqrt(delta);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) if (nthreads != 1)
+#endif
+    for (int64_t i = 0; i < M; ++i) {
+        double sum = 0.0, comp = 0.0;
+        for (int64_t j = 0; j < N; ++j)
+            neumaier_add(&sum, &comp, alpha[j] * soe_kernel(n_e, tre, tim, wre, wim, x[i] - y[j], sd));
+        u[i] = sum + comp;
+    }
+}
+
+/* ---- O3: the paper's algorithm ------------------------------------------------------ */
+
+/* Merged point q: q < N is source j = q (coordinate y[q]); q >= N is target i = q - N. */
+typedef struct {
+    const double* x;
+    const double* y;
+    int64_t N;
+} merged_t;
+
+static inline double merged_coord(const merged_t* m, int64_t q) {
+    return q < m->N ? m->y[q] : m->x[q - m->N];
+}
+
+/* Stable merge sort of merged indices by coordinate (ties keep the merged order). */
+static void merge_sort(int64_t* a, int64_t* tmp, int64_t n, const merged_t* m) {
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) {
+                /* take from the right run only if strictly smaller: stability */
+                if (merged_coord(m, a[j]) < merged_coord(m, a[i])) tmp[k++] = a[j++];
+                else tmp[k++] = a[i++];
+            }
+            while (i < mid) tmp[k++] = a[i++];
+            while (j < hi) tmp[k++] = a[j++];
+        }
+        memcpy(a, tmp, (size_t)n * sizeof(int64_t));
+    }
+}
+
+/* Sorted merged permutation (bit-exact reference for the GPU sort).
+ * Returns 0, or -1 if a coordinate is NaN or infinite, -2 on allocation failure. */
+int o3_sort_merged(const double* x, int64_t M, const double* y, int64_t N, int64_t* perm) {
+    int64_t P = M + N;
+    merged_t m = {x, y, N};
+    for (int64_t q = 0; q < P; ++q) {
+        if (!isfinite(merged_coord(&m, q))) return -1;
+        perm[q] = q;
+    }
+    int64_t* tmp = (int64_t*)malloc((size_t)(P > 0 ? P : 1) * sizeof(int64_t));
+    if (!tmp) return -2;
+    merge_sort(perm, tmp, P, &m);
+    free(tmp);
+    return 0;
+}
+
+/* O3: sort, forward pass (eq. 4.5), backward pass (eq. 4.6), evaluation (eq. 4.1),
+ * unpermute.  exact_self != 0 adds (1 - S_n(0)) alpha_j for every source that shares
+ * the coordinate of a target, so that coincident pairs get G(0) = 1 instead of S_n(0).
+ * perm_out (may be NULL) receives the sorted merged order.  Returns 0 or the error of
+ * o3_sort_merged. */
+int o3_recurrence(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                  double delta, int n_e, const double* tre, const double* tim, const double* wre,
+                  const double* wim, int exact_self, double* u, int64_t* perm_out) {
+    int64_t P = M + N;
+    if (n_e < 1 || n_e > ORACLE_MAX_TERMS) return -3;
+    int64_t* perm = perm_out ? perm_out : (int64_t*)malloc((size_t)(P > 0 ? P : 1) * sizeof(int64_t));
+    if (!perm) return -2;
+    int rc = o3_sort_merged(x, M, y, N, perm);
+    if (rc) {
+        if (!perm_out) free(perm);
+        return rc;
+    }
+    merged_t m = {x, y, N};
+    const double sd = sqrt(delta);
+    double* hre = (double*)calloc((size_t)(M > 0 ? M : 1) * n_e, sizeof(double)); /* h^+ at targets */
+    double* him = (double*)calloc((size_t)(M > 0 ? M : 1) * n_e, sizeof(double));
+    if (!hre || !him) { free(hre); free(him); if (!perm_out) free(perm); return -2; }
+    double Fr[ORACLE_MAX_TERMS], Fi[ORACLE_MAX_TERMS];
+    for (int k = 0; k < n_e; ++k) Fr[k] = Fi[k] = 0.0;
+    /* forward: h^+_p = e^{-t_k (z_p - z_{p-1}) / sqrt(delta)} h^+_{p-1} + alpha_p [source] */
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t q = perm[p];
+        double z = merged_coord(&m, q);
+        if (p > 0) {
+            double gap = z - merged_coord(&m, perm[p - 1]);
+            for (int k = 0; k < n_e; ++k) {
+                double mag = exp(-tre[k] * gap / sd), ang = tim[k] * gap / sd;
+                double er = mag * cos(ang), ei = -mag * sin(ang);
+                double nr = er * Fr[k] - ei * Fi[k], ni = er * Fi[k] + ei * Fr[k];
+                Fr[k] = nr; Fi[k] = ni;
+            }
+        }
+        if (q < N) {
+            for (int k = 0; k < n_e; ++k) Fr[k] += alpha[q];
+        } else {
+            int64_t i = q - N;
+            for (int k = 0; k < n_e; ++k) { hre[i * n_e + k] = Fr[k]; him[i * n_e + k] = Fi[k]; }
+        }
+    }
+    /* backward: h^-_p = e^{-t_k (z_{p+1} - z_p) / sqrt(delta)} (h^-_{p+1} + alpha_{p+1} [source]) */
+    double Br[ORACLE_MAX_TERMS], Bi[ORACLE_MAX_TERMS];
+    for (int k = 0; k < n_e; ++k) Br[k] = Bi[k] = 0.0;
+    double s0 = 0.0;
+    for (int k = 0; k < n_e; ++k) s0 += wre[k];
+    for (int64_t p = P - 1; p >= 0; --p) {
+        int64_t q = perm[p];
+        if (q >= N) {
+            int64_t i = q - N;
+            double acc = 0.0;
+            for (int k = 0; k < n_e; ++k)
+                acc += wre[k] * (hre[i * n_e + k] + Br[k]) - wim[k] * (him[i * n_e + k] + Bi[k]);
+            if (exact_self) {
+                /* sources that share this coordinate sit just before the target run */
+                double zi = x[i], same = 0.0;
+                for (int64_t r = p - 1; r >= 0 && merged_coord(&m, perm[r]) == zi; --r)
+                    if (perm[r] < N) same += alpha[perm[r]];
+                acc += (1.0 - s0) * same;
+            }
+            u[i] = acc;
+        } else {
+            for (int k = 0; k < n_e; ++k) Br[k] += alpha[q];
+        }
+        if (p > 0) {
+            double gap = merged_coord(&m, q) - merged_coord(&m, perm[p - 1]);
+            for (int k = 0; k < n_e; ++k) {
+                double mag = exp(-tre[k] * gap / sd), ang = tim[k] * gap / sd;
+                double er = mag * cos(ang), ei = -mag * sin(ang);
+                double nr = er * Br[k] - ei * Bi[k], ni = er * Bi[k] + ei * Br[k];
+                Br[k] = nr; Bi[k] = ni;
+            }
+        }
+    }
+    free(hre); free(him);
+    if (!perm_out) free(perm);
+    return 0;
+}
+
+/* ---- direct gradients ------------------------------------------------------------------
+ * L = sum_i g_i u_i.  For a kernel K(d), d = x_i - y_j:
+ *   dL/dalpha_j = sum_i g_i K(d);  dL/dx_i = g_i sum_j alpha_j K'(d);
+ *   dL/dy_j = -alpha_j sum_i g_i K'(d);  dL/ddelta = sum_ij g_i alpha_j dK/ddelta.
+ * Gaussian: K = e^{-d^2/(4 delta)}, K' = -d/(2 delta) K, dK/ddelta = d^2/(4 delta^2) K.
+ * SOE: K = Re sum W_k e^{-tau_k s |d|}, s = delta^{-1/2};
+ *   K' = Re sum W_k (-tau_k s sgn d) e^{...} with sgn 0 = 0 (the cusp at d = 0 is given
+ *   the symmetric value 0, which is also G'(0));
+ *   dK/ddelta = Re sum W_k tau_k |d| s / (2 delta) e^{...}.
+ */
+void o1_grad(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+             double delta, const double* g, double* gx, double* gy, double* galpha, double* gdelta) {
+    double gd = 0.0;
+    for (int64_t j = 0; j < N; ++j) { gy[j] = 0.0; galpha[j] = 0.0; }
+    for (int64_t i = 0; i < M; ++i) {
+        double sx = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double d = x[i] - y[j];
+            double K = exp(-(d * d) / (4.0 * delta));
+            double Kp = -d / (2.0 * delta) * K;
+            galpha[j] += g[i] * K;
+            sx += alpha[j] * Kp;
+            gy[j] -= alpha[j] * g[i] * Kp;
+            gd += g[i] * alpha[j] * (d * d) / (4.0 * delta * delta) * K;
+        }
+        gx[i] = g[i] * sx;
+    }
+    *gdelta = gd;
+}
+
+void o2_grad(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+             double delta, int n_e, const double* tre, const double* tim, const double* wre,
+             const double* wim, const double* g, double* gx, double* gy, double* galpha,
+             double* gdelta) {
+    const double s = 1.0 / sqrt(delta);
+    double gd = 0.0;
+    for (int64_t j = 0; j < N; ++j) { gy[j] = 0.0; galpha[j] = 0.0; }
+    for (int64_t i = 0; i < M; ++i) {
+        double sx = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double d = x[i] - y[j];
+            double r = fabs(d) * s;
+            double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
+            double K = 0.0, Kp = 0.0, Kd = 0.0;
+            for (int k = 0; k < n_e; ++k) {
+                double mag = exp(-tre[k] * r);
+                double er = mag * cos(tim[k] * r), ei = -mag * sin(tim[k] * r); /* e^{-tau r} */
+                double wer = wre[k] * er - wim[k] * ei, wei = wre[k] * ei + wim[k] * er; /* W e^{-tau r} */
+                K += wer;
+                /* Re(W tau e^{-tau r}) */
+                double wt = wer * tre[k] - wei * tim[k];
+                Kp += -s * sg * wt;
+                Kd += wt * fabs(d) * s / (2.0 * delta);
+            }
+            galpha[j] += g[i] * K;
+            sx += alpha[j] * Kp;
+            gy[j] -= alpha[j] * g[i] * Kp;
+            gd += g[i] * alpha[j] * Kd;
+        }
+        gx[i] = g[i] * sx;
+    }
+    *gdelta = gd;
+}

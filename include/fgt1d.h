@@ -1,0 +1,144 @@
+/*
+ * fgt1d.h -- C ABI of the GB300 (sm_103a) sum-of-exponentials fast Gauss transform.
+ *
+ * The transform (eqs. 1.1-1.2 of Jiang, "A fast Gauss transform in one dimension
+ * using sum-of-exponentials approximations", arXiv:1909.09825):
+ *
+ *     u_i = sum_{j=1..N} exp(-(x_i - y_j)^2 / (4 delta)) alpha_j,   i = 1..M,
+ *
+ * is evaluated with the SOE approximation of eq. 1.3,
+ *     G(x; delta) ~ S_n(x; delta) = Re sum_{k=1..n_e} W_k exp(-tau_k |x| / sqrt(delta)),
+ * (n_e = n/2 conjugate pairs, W_k = 2 w_k; Sec. 4), whose nodes come from the
+ * Caratheodory-Fejer near-best rational approximation of e^z on (-inf, 0]
+ * (Sec. 2.3, eqs. 2.10-2.14; Sec. 3.3).  The sources and targets are merged and
+ * sorted (Sec. 4) and the split sums h+ / h- of eqs. 4.3-4.4 are swept with the
+ * forward and backward recurrences of eqs. 4.5-4.6, then evaluated (eq. 4.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays named x, y, alpha, u, grad_* and perm are DEVICE pointers unless the
+ *    name ends in _host; they are owned by the caller, contiguous, float64
+ *    (perm: uint32).  They must stay valid until the stream work completes.
+ *  - Merged order: the merged point q < N is source j = q (coordinate y[q]);
+ *    q >= N is target i = q - N (coordinate x[q - N]).  The stable sort orders by
+ *    coordinate, ties by q, so a source equal to a target precedes it and is
+ *    counted in h+ (eq. 4.4 uses y_j <= x_i).  -0.0 is treated as +0.0.
+ *  - `workspace` is a caller-allocated device buffer of at least the size returned
+ *    by the matching *_workspace_size call, 256-byte aligned.  One workspace must
+ *    not be used by two calls that can overlap on the GPU.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute entry
+ *    points are asynchronous: they enqueue work and return.  Argument errors are
+ *    returned immediately; conditions found on the device (a NaN/Inf coordinate,
+ *    an expired bounded wait) are recorded in the workspace and returned by
+ *    fgt1d_check, which synchronises the stream.
+ *  - Return value: FGT1D_OK (0) or one of the FGT1D_E* codes below.
+ *  - P = M + N must be below 2^31.  M = 0 is a no-op; N = 0 writes u = 0.
+ */
+#ifndef FGT1D_H
+#define FGT1D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fgt1d_plan_s* fgt1d_plan; /* opaque, host memory owned by the library */
+typedef void* fgt1d_stream;              /* a cudaStream_t */
+
+/* status codes */
+#define FGT1D_OK 0
+#define FGT1D_EINVAL 1        /* bad argument: delta <= 0 or not finite, eps out of range,
+                                 negative size, P >= 2^31, NULL pointer with nonzero size */
+#define FGT1D_EUNSUPPORTED 2  /* eps below the smallest E_n reachable, or FP32 with eps < 1e-6 */
+#define FGT1D_ENONFINITE 3    /* a coordinate was NaN or infinite (found on the device) */
+#define FGT1D_ENOMEM 4        /* host allocation failed */
+#define FGT1D_ETIMEOUT 5      /* a bounded inter-block wait gave up (found on the device) */
+#define FGT1D_ECUDA 6         /* a CUDA runtime call failed */
+#define FGT1D_EWORKSPACE 7    /* workspace NULL, misaligned or smaller than required */
+
+/* plan flags */
+#define FGT1D_FP64 0u         /* every step in FP64 */
+#define FGT1D_FP32 1u         /* bulk recurrences in FP32 complex, FP64 coordinate differences
+                                 and inter-tile carries; requires eps >= 1e-6 */
+
+#define FGT1D_MAX_TERMS 8     /* largest n_e a plan can hold */
+#define FGT1D_MAX_N 14        /* largest CF order n built in FP64 (Sec. 3.3) */
+
+/* Step a0, the SOE generator (Sec. 2.3 eqs. 2.10-2.13, Sec. 3.3; eq. 3.1 for E_n).
+ * Builds the CF type (n-1, n) approximation of e^z on (-inf, 0] for even n in
+ * [2, FGT1D_MAX_N] in FP64 on the host and converts it with eq. 2.11.
+ * Outputs: *n_e = n/2; tau_k = sqrt(z_k) (one of each conjugate pair, Im tau_k > 0,
+ * ascending Re tau_k, delta-free) and W_k = 2 w_k in caller host arrays of length
+ * >= FGT1D_MAX_TERMS; *E_n = max |G(x;1) - S_n(x;1)| over the sampled grid (x = 0,
+ * 1e5 log-spaced points in [1e-5, 1e2], and uniform grids on [0, 12] and [0, 1e-3]).
+ * Errors: FGT1D_EINVAL for odd or out-of-range n or NULL outputs. */
+int fgt1d_soe_cf(int n, int* n_e, double* tau_re, double* tau_im, double* w_re, double* w_im,
+                 double* E_n);
+
+/* Plan for bandwidth delta and accuracy eps: picks the smallest even n with
+ * E_n <= eps (Sec. 3.3), keeps half of the conjugate pairs (Sec. 4) and
+ * precomputes the per-term constants.  flags: FGT1D_FP64 or FGT1D_FP32.
+ * Errors: FGT1D_EINVAL (delta <= 0/non-finite, eps not in (0, 0.5), unknown flags,
+ * out == NULL), FGT1D_EUNSUPPORTED (eps < E_n of FGT1D_MAX_N, or FP32 with eps < 1e-6),
+ * FGT1D_ENOMEM. */
+int fgt1d_plan_create(double delta, double eps, unsigned flags, fgt1d_plan* out);
+
+/* Plan from a caller-given halved SOE (tau_k, W_k), k < n_e <= FGT1D_MAX_TERMS, with
+ * Re tau_k > 0 (so every multiplier has modulus <= 1, eq. 2.3).  Used to run the
+ * transform with any SOE, e.g. the hyperbolic-contour one of Sec. 3.4.  E_n is
+ * recorded as NaN (unknown).  Errors as fgt1d_plan_create, plus FGT1D_EINVAL for
+ * Re tau_k <= 0 or non-finite values. */
+int fgt1d_plan_create_soe(double delta, int n_e, const double* tau_re, const double* tau_im,
+                          const double* w_re, const double* w_im, unsigned flags, fgt1d_plan* out);
+
+/* Reads a plan back.  Any output pointer may be NULL; the node arrays need room for
+ * n_e values.  *n is the CF order (0 for a plan built from a given SOE). */
+int fgt1d_plan_info(fgt1d_plan plan, int* n, int* n_e, double* E_n, double* delta,
+                    unsigned* flags, double* tau_re, double* tau_im, double* w_re, double* w_im);
+
+void fgt1d_plan_destroy(fgt1d_plan plan);
+
+/* Device workspace bytes needed by fgt1d_execute for these sizes. */
+int fgt1d_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes);
+
+/* Steps a1-a7 (Sec. 4): the transform of eq. 1.1 for device arrays x[M] (targets),
+ * y[N] (sources), alpha[N]; writes u[M] in the original target order.  Stream-ordered;
+ * device-side errors are reported by fgt1d_check. */
+int fgt1d_execute(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                  const double* alpha, int64_t N, double* u, void* workspace, size_t ws_bytes,
+                  fgt1d_stream stream);
+
+/* Same transform for HOST arrays (pageable or pinned): copies x, y, alpha to the
+ * device, runs fgt1d_execute, copies u back and synchronises the stream.  The
+ * workspace (device) must hold fgt1d_workspace_size_host bytes; it also carries the
+ * device copies of the inputs and output.  Returns the device status like fgt1d_check. */
+int fgt1d_workspace_size_host(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes);
+int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
+                       const double* alpha_host, int64_t N, double* u_host, void* workspace,
+                       size_t ws_bytes, fgt1d_stream stream);
+
+/* Steps a1-a2 alone (Sec. 4, first step; Sec. 5 sorting): the stable sort of the
+ * merged points.  perm[p] (device, uint32, length M + N) receives the merged index at
+ * sorted position p.  Workspace from fgt1d_sort_workspace_size. */
+int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes);
+int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,
+                      void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
+/* Synchronises `stream`, then returns and clears the device status recorded in the
+ * workspace by the previous compute calls: FGT1D_OK, FGT1D_ENONFINITE, FGT1D_ETIMEOUT,
+ * or FGT1D_ECUDA if the stream reported an error. */
+int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
+/* Human-readable text of a status code (static storage). */
+const char* fgt1d_strerror(int status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int fgt1d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGT1D_H */

@@ -1,0 +1,284 @@
+// C ABI entry points: argument checks, workspace layout, launch sequence.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "fgt1d_internal.h"
+#include "kernels.h"
+
+namespace fgt1d {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Workspace layout.  [0, zero_end) is cleared at the start of every call.
+struct Layout {
+    size_t header = 0;       // status (u32 at 0), sort tile counters (8 u32 at 32),
+                             // sweep tile counters (2 u32 at 64), SortPlan at 128
+    size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;
+    size_t zero_end = 0;
+    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0;
+    size_t hx = 0, hy = 0, ha = 0, hu = 0;
+    size_t total = 0;
+    int64_t sort_tiles = 0, sweep_tiles = 0;
+};
+
+Layout make_layout(int64_t M, int64_t N, int n_e, unsigned flags, bool sweeps, bool host) {
+    Layout L;
+    const int64_t P = M + N;
+    L.sort_tiles = (P + kSortTile - 1) / kSortTile;
+    const int tile = (flags & FGT1D_FP32) ? sweep_tile_f32() : sweep_tile_f64();
+    L.sweep_tiles = sweeps ? (P + tile - 1) / tile : 0;
+    size_t off = 0;
+    L.header = off; off += align_up(256);
+    L.hist = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256);
+    L.offs = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256);
+    L.sort_desc = off; off += align_up(sizeof(uint64_t) * kSortDigits * (size_t)L.sort_tiles * 256);
+    L.fdesc = off; off += align_up(sizeof(TileDesc) * (size_t)L.sweep_tiles * (size_t)n_e);
+    L.bdesc = off; off += align_up(sizeof(TileDesc) * (size_t)L.sweep_tiles * (size_t)n_e);
+    L.zero_end = off;
+    L.keysA = off; off += align_up(sizeof(uint64_t) * (size_t)P);
+    L.keysB = off; off += align_up(sizeof(uint64_t) * (size_t)P);
+    L.valsA = off; off += align_up(sizeof(uint32_t) * (size_t)P);
+    L.valsB = off; off += align_up(sizeof(uint32_t) * (size_t)P);
+    if (sweeps) {
+        if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * (size_t)P); }
+        L.fwd = off; off += align_up(sizeof(double) * (size_t)P);
+    }
+    if (host) {
+        L.hx = off; off += align_up(sizeof(double) * (size_t)M);
+        L.hy = off; off += align_up(sizeof(double) * (size_t)N);
+        L.ha = off; off += align_up(sizeof(double) * (size_t)N);
+        L.hu = off; off += align_up(sizeof(double) * (size_t)M);
+    }
+    L.total = off;
+    return L;
+}
+
+bool sizes_ok(int64_t M, int64_t N) {
+    return M >= 0 && N >= 0 && M + N < (int64_t(1) << 31);
+}
+
+int ws_ok(const void* ws, size_t ws_bytes, const Layout& L) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0 || ws_bytes < L.total) return FGT1D_EWORKSPACE;
+    return FGT1D_OK;
+}
+
+SortArgs sort_args(const double* x, int64_t M, const double* y, int64_t N, char* ws, const Layout& L) {
+    SortArgs a;
+    a.x = x;
+    a.y = y;
+    a.N = N;
+    a.P = M + N;
+    a.keysA = reinterpret_cast<uint64_t*>(ws + L.keysA);
+    a.keysB = reinterpret_cast<uint64_t*>(ws + L.keysB);
+    a.valsA = reinterpret_cast<uint32_t*>(ws + L.valsA);
+    a.valsB = reinterpret_cast<uint32_t*>(ws + L.valsB);
+    a.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+    a.offs = reinterpret_cast<uint32_t*>(ws + L.offs);
+    a.plan = reinterpret_cast<SortPlan*>(ws + L.header + 128);
+    a.desc = reinterpret_cast<uint64_t*>(ws + L.sort_desc);
+    a.desc_stride = (size_t)L.sort_tiles * 256;
+    a.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 32);
+    a.status = reinterpret_cast<uint32_t*>(ws + L.header);
+    return a;
+}
+
+// Host-side constants of the sweep kernels (Taylor coefficients and thresholds).
+SweepConsts make_consts(const fgt1d_plan_s& p) {
+    SweepConsts c;
+    std::memset(&c, 0, sizeof(c));
+    c.n_e = p.n_e;
+    c.s = 1.0 / std::sqrt(p.delta);
+    const double u64 = std::ldexp(1.0, -56), u32 = std::ldexp(1.0, -27);
+    for (int k = 0; k < p.n_e; ++k) {
+        c.tau_re[k] = p.tau_re[k];
+        c.tau_im[k] = p.tau_im[k];
+        c.w_re[k] = p.w_re[k];
+        c.w_im[k] = p.w_im[k];
+        c.tauf_re[k] = (float)p.tau_re[k];
+        c.tauf_im[k] = (float)p.tau_im[k];
+        // (-tau)^j / j!
+        long double ar = 1.0L, ai = 0.0L;
+        for (int j = 0; j <= kTaylorMax; ++j) {
+            c.tc_re[k][j] = (double)ar;
+            c.tc_im[k][j] = (double)ai;
+            c.tcf_re[k][j] = (float)ar;
+            c.tcf_im[k][j] = (float)ai;
+            long double nr = (ar * -p.tau_re[k] - ai * -p.tau_im[k]) / (j + 1);
+            long double ni = (ar * -p.tau_im[k] + ai * -p.tau_re[k]) / (j + 1);
+            ar = nr;
+            ai = ni;
+        }
+        // degree d is enough while (|tau| theta)^d / (d+1)! <= u: the truncation error of
+        // each multiplier stays below u times its first-order term, so it cannot
+        // accumulate past u times the total decay along a sweep.
+        const double at = std::hypot(p.tau_re[k], p.tau_im[k]);
+        double fact = 1.0;
+        for (int d = 0; d <= kTaylorMax; ++d) {
+            fact *= (d + 1);
+            if (d == 0) {
+                c.theta_hi_lim[k][0] = 0;
+                c.theta_hi_lim_f[k][0] = 0;
+                continue;
+            }
+            double th64 = std::pow(fact * u64, 1.0 / d) / at;
+            double th32 = std::pow(fact * u32, 1.0 / d) / at;
+            uint64_t b64;
+            std::memcpy(&b64, &th64, 8);
+            c.theta_hi_lim[k][d] = (uint32_t)(b64 >> 32) - 1u;
+            float f32 = (float)th32;
+            uint32_t b32;
+            std::memcpy(&b32, &f32, 4);
+            c.theta_hi_lim_f[k][d] = b32 - 1u;
+        }
+    }
+    return c;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
+
+int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                  double* u, char* ws, const Layout& L, cudaStream_t st) {
+    if (M == 0) return FGT1D_OK;
+    if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, st);
+    if (e != cudaSuccess) return FGT1D_ECUDA;
+    SortArgs sa = sort_args(x, M, y, N, ws, L);
+    e = launch_sort(sa, st);
+    if (e != cudaSuccess) return FGT1D_ECUDA;
+    SweepArgs w;
+    w.P = M + N;
+    w.N = N;
+    w.keysA = sa.keysA;
+    w.keysB = sa.keysB;
+    w.valsA = sa.valsA;
+    w.valsB = sa.valsB;
+    w.plan = sa.plan;
+    w.alpha = alpha;
+    w.mult = L.mult ? reinterpret_cast<double2*>(ws + L.mult) : nullptr;
+    w.fwd = reinterpret_cast<double*>(ws + L.fwd);
+    w.u = u;
+    w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
+    w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
+    w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
+    w.status = sa.status;
+    w.tiles = L.sweep_tiles;
+    SweepConsts c = make_consts(p);
+    e = (p.flags & FGT1D_FP32) ? launch_sweeps_f32(w, c, st) : launch_sweeps_f64(w, c, st);
+    return cuda_status(e);
+}
+
+}  // namespace
+}  // namespace fgt1d
+
+using namespace fgt1d;
+
+extern "C" int fgt1d_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
+    if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, false).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_workspace_size_host(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
+    if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, true).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes) {
+    if (!bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    *bytes = make_layout(M, N, 1, FGT1D_FP64, false, false).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_execute(fgt1d_plan plan, const double* x, int64_t M, const double* y, const double* alpha,
+                             int64_t N, double* u, void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    if (M > 0 && (!x || !u)) return FGT1D_EINVAL;
+    if (N > 0 && M > 0 && (!y || !alpha)) return FGT1D_EINVAL;
+    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false);
+    if (M > 0 && N > 0) {
+        int r = ws_ok(workspace, ws_bytes, L);
+        if (r) return r;
+    }
+    return run_transform(*plan, x, M, y, alpha, N, u, static_cast<char*>(workspace), L,
+                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
+                                  const double* alpha_host, int64_t N, double* u_host, void* workspace,
+                                  size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    if (M > 0 && (!x_host || !u_host)) return FGT1D_EINVAL;
+    if (N > 0 && M > 0 && (!y_host || !alpha_host)) return FGT1D_EINVAL;
+    if (M == 0) return FGT1D_OK;
+    if (N == 0) {
+        std::memset(u_host, 0, sizeof(double) * (size_t)M);
+        return FGT1D_OK;
+    }
+    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, true);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* dx = reinterpret_cast<double*>(ws + L.hx);
+    double* dy = reinterpret_cast<double*>(ws + L.hy);
+    double* da = reinterpret_cast<double*>(ws + L.ha);
+    double* du = reinterpret_cast<double*>(ws + L.hu);
+    if (cudaMemcpyAsync(dx, x_host, sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dy, y_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(da, alpha_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FGT1D_ECUDA;
+    r = run_transform(*plan, dx, M, dy, da, N, du, ws, L, st);
+    if (r) return r;
+    if (cudaMemcpyAsync(u_host, du, sizeof(double) * (size_t)M, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FGT1D_ECUDA;
+    return fgt1d_check(workspace, ws_bytes, stream);
+}
+
+extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,
+                                 void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    if (!sizes_ok(M, N)) return FGT1D_EINVAL;
+    if ((M > 0 && !x) || (N > 0 && !y) || (M + N > 0 && !perm)) return FGT1D_EINVAL;
+    if (M + N == 0) return FGT1D_OK;
+    Layout L = make_layout(M, N, 1, FGT1D_FP64, false, false);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, L.zero_end, st) != cudaSuccess) return FGT1D_ECUDA;
+    SortArgs sa = sort_args(x, M, y, N, ws, L);
+    if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
+    return cuda_status(launch_copy_perm(sa, perm, st));
+}
+
+extern "C" int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FGT1D_ECUDA;
+    if (!workspace || ws_bytes < sizeof(uint32_t)) return FGT1D_EWORKSPACE;
+    uint32_t status = 0;
+    if (cudaMemcpy(&status, workspace, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess) return FGT1D_ECUDA;
+    if (status && cudaMemset(workspace, 0, sizeof(status)) != cudaSuccess) return FGT1D_ECUDA;
+    if (status & kStatusNonFinite) return FGT1D_ENONFINITE;
+    if (status & kStatusTimeout) return FGT1D_ETIMEOUT;
+    return FGT1D_OK;
+}
+
+extern "C" const char* fgt1d_strerror(int status) {
+    switch (status) {
+        case FGT1D_OK: return "ok";
+        case FGT1D_EINVAL: return "invalid argument";
+        case FGT1D_EUNSUPPORTED: return "unsupported accuracy or precision";
+        case FGT1D_ENONFINITE: return "a coordinate is NaN or infinite";
+        case FGT1D_ENOMEM: return "host allocation failed";
+        case FGT1D_ETIMEOUT: return "a bounded inter-block wait expired";
+        case FGT1D_ECUDA: return "CUDA runtime error";
+        case FGT1D_EWORKSPACE: return "workspace missing, misaligned or too small";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int fgt1d_version(void) { return 100; }

@@ -1,0 +1,46 @@
+// Internal declarations shared by the host plan code and the CUDA kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/fgt1d.h"
+
+struct fgt1d_plan_s {
+    int n;              // CF order (0 when built from a caller SOE)
+    int n_e;            // number of kept conjugate-pair terms
+    double delta;
+    double E_n;
+    unsigned flags;
+    double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
+    double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
+};
+
+namespace fgt1d {
+
+// Device status bits recorded in the workspace header.
+enum : uint32_t {
+    kStatusNonFinite = 1u,
+    kStatusTimeout = 2u,
+};
+
+// Degree limit of the per-point Taylor multiplier e^{-tau theta} and the number of
+// thresholds kept per plan.
+constexpr int kTaylorMax = 12;
+
+// Per-launch constants of the sweep kernels (passed by value).
+struct SweepConsts {
+    int n_e;
+    double s;                       // 1 / sqrt(delta)
+    double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
+    double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
+    // Taylor coefficients (-tau_k)^j / j!, j = 0..kTaylorMax, per term
+    double tc_re[FGT1D_MAX_TERMS][kTaylorMax + 1], tc_im[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    float tcf_re[FGT1D_MAX_TERMS][kTaylorMax + 1], tcf_im[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    float tauf_re[FGT1D_MAX_TERMS], tauf_im[FGT1D_MAX_TERMS];
+    // theta thresholds: Taylor degree d is enough (FP64) while theta <= theta_lim[d];
+    // stored as the high 32 bits of the double so that warps compare them as integers.
+    uint32_t theta_hi_lim[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    uint32_t theta_hi_lim_f[FGT1D_MAX_TERMS][kTaylorMax + 1];   // same for the FP32 path (float bits)
+};
+
+}  // namespace fgt1d

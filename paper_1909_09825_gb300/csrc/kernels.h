@@ -1,0 +1,80 @@
+// Launch-side declarations of the CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fgt1d_internal.h"
+
+namespace fgt1d {
+
+// ---- sort (steps a1-a2) ----
+constexpr int kSortDigits = 8;      // 8-bit digits of a 64-bit key
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 16;
+constexpr int kSortTile = kSortThreads * kSortIPT;
+// Upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at 2 GHz).
+constexpr long long kSpinLimitCycles = 4000000000LL;
+
+struct SortPlan {
+    uint32_t active[kSortDigits];
+    int32_t src[kSortDigits];   // -1: keys generated from x/y; 0: buffer A; 1: buffer B
+    int32_t dst[kSortDigits];
+    int32_t final_buf;          // buffer (0 = A, 1 = B) that holds the sorted keys/indices
+};
+
+struct SortArgs {
+    const double* x;
+    const double* y;
+    int64_t N, P;
+    uint64_t* keysA;
+    uint64_t* keysB;
+    uint32_t* valsA;
+    uint32_t* valsB;
+    uint32_t* hist;       // [8][256]
+    uint32_t* offs;       // [8][256]
+    SortPlan* plan;
+    uint64_t* desc;       // [8][desc_stride] look-back words
+    size_t desc_stride;   // tiles * 256
+    uint32_t* tile_ctr;   // [8]
+    uint32_t* status;
+};
+
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
+
+// ---- sweeps (steps a3-a7) ----
+struct TileDesc {           // one (tile, term) entry of the decoupled look-back
+    double agg_re, agg_im;  // tile aggregate (zero carry)
+    double inc_re, inc_im;  // inclusive value (all carries)
+    double z;               // anchor coordinate (last point: forward; first point: backward)
+    uint32_t flag;          // 0 none, 1 aggregate, 2 inclusive
+    uint32_t pad;
+};
+
+struct SweepArgs {
+    int64_t P, N;
+    const uint64_t* keysA;
+    const uint64_t* keysB;
+    const uint32_t* valsA;
+    const uint32_t* valsB;
+    const SortPlan* plan;
+    const double* alpha;
+    double2* mult;          // [n_e][P] multiplier table (FP64 path) or nullptr
+    double* fwd;            // [P] forward partial sums Re sum_k W_k h+_k at targets
+    double* u;              // [M] output
+    TileDesc* fdesc;        // [tiles][n_e]
+    TileDesc* bdesc;        // [tiles][n_e]
+    uint32_t* tile_ctr;     // [2]
+    uint32_t* status;
+    int64_t tiles;
+};
+
+int sweep_tile_f64();  // points per sweep tile
+int sweep_tile_f32();
+cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
+cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
+
+// copies the sorted merged indices (final sort buffer) to perm
+cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st);
+
+}  // namespace fgt1d

@@ -1,0 +1,171 @@
+"""Python binding of libfgt1d (argument marshalling only; torch provides device memory
+and streams).  Every step of the transform runs in the CUDA library."""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+
+def _f64_host(a, n):
+    out = np.zeros(n, dtype=np.float64)
+    out[: len(a)] = a
+    return out
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def soe_cf(n):
+    """SOE of the CF order-n approximation (step a0): (tau, W, E_n) with tau, W complex
+    arrays of length n/2 (one node of each conjugate pair, W = 2 w)."""
+    ne = ctypes.c_int()
+    arr = [np.zeros(_lib.MAX_TERMS) for _ in range(4)]
+    En = ctypes.c_double()
+    check(lib().fgt1d_soe_cf(int(n), ctypes.byref(ne), *[_ptr(a) for a in arr], ctypes.byref(En)), "soe_cf")
+    k = ne.value
+    return arr[0][:k] + 1j * arr[1][:k], arr[2][:k] + 1j * arr[3][:k], En.value
+
+
+class Plan:
+    """A transform plan for bandwidth delta and accuracy eps (or a given SOE).
+
+    precision: "fp64" (every step in FP64) or "fp32" (FP32-complex recurrences with
+    FP64 coordinate differences and inter-tile carries; eps >= 1e-6).
+    """
+
+    def __init__(self, delta, eps=None, precision="fp64", soe=None):
+        if precision not in ("fp64", "fp32"):
+            raise ValueError(precision)
+        flags = _lib.FGT1D_FP32 if precision == "fp32" else _lib.FGT1D_FP64
+        h = ctypes.c_void_p()
+        if soe is None:
+            check(lib().fgt1d_plan_create(float(delta), float(eps), flags, ctypes.byref(h)), "plan_create")
+        else:
+            tau, W = (np.asarray(v, dtype=complex) for v in soe)
+            k = len(tau)
+            a = [np.ascontiguousarray(v, dtype=np.float64) for v in (tau.real, tau.imag, W.real, W.imag)]
+            check(lib().fgt1d_plan_create_soe(float(delta), k, *[_ptr(v) for v in a], flags, ctypes.byref(h)),
+                  "plan_create_soe")
+        self._h = h
+        self.precision = precision
+        n, ne, En, d, fl = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_uint()
+        arr = [np.zeros(_lib.MAX_TERMS) for _ in range(4)]
+        check(lib().fgt1d_plan_info(h, ctypes.byref(n), ctypes.byref(ne), ctypes.byref(En), ctypes.byref(d),
+                                    ctypes.byref(fl), *[_ptr(v) for v in arr]), "plan_info")
+        self.n, self.n_e, self.E_n, self.delta = n.value, ne.value, En.value, d.value
+        k = self.n_e
+        self.tau = arr[0][:k] + 1j * arr[1][:k]
+        self.W = arr[2][:k] + 1j * arr[3][:k]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_size(self, M, N, host=False):
+        b = ctypes.c_size_t()
+        f = lib().fgt1d_workspace_size_host if host else lib().fgt1d_workspace_size
+        check(f(self._h, int(M), int(N), ctypes.byref(b)), "workspace_size")
+        return b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().fgt1d_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+class Workspace:
+    """Grow-only device workspace (a torch uint8 buffer) reused across calls."""
+
+    def __init__(self, device="cuda"):
+        self.device = torch.device(device)
+        self.buf = None
+
+    def get(self, nbytes):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    return t
+
+
+_default_ws = {}
+
+
+def _workspace(ws, device, nbytes):
+    if ws is None:
+        key = torch.device(device).index
+        ws = _default_ws.setdefault(key, Workspace(device))
+    return ws.get(nbytes)
+
+
+def transform(plan, x, y, alpha, out=None, workspace=None, stream=None, sync_check=True):
+    """u = sum_j exp(-(x_i - y_j)^2 / (4 delta)) alpha_j on the GPU (eq. 1.1).
+
+    x (M,), y (N,), alpha (N,): contiguous float64 CUDA tensors.  Returns u (M,).
+    With sync_check the stream is synchronised and device-side errors raise."""
+    _dev(x, "x"), _dev(y, "y"), _dev(alpha, "alpha")
+    M, N = x.numel(), y.numel()
+    if alpha.numel() != N:
+        raise ValueError("alpha and y differ in length")
+    if out is None:
+        out = torch.empty(M, dtype=torch.float64, device=x.device)
+    _dev(out, "out")
+    nbytes = plan.workspace_size(M, N)
+    ws = _workspace(workspace, x.device, nbytes)
+    st = _stream_ptr(stream)
+    check(lib().fgt1d_execute(plan.handle, ctypes.c_void_p(x.data_ptr()), M, ctypes.c_void_p(y.data_ptr()),
+                              ctypes.c_void_p(alpha.data_ptr()), N, ctypes.c_void_p(out.data_ptr()),
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "execute")
+    if sync_check:
+        check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "execute (device)")
+    return out
+
+
+def execute_host(plan, x, y, alpha, out=None, workspace=None, stream=None):
+    """End-to-end transform of HOST numpy arrays through fgt1d_execute_host (copies in,
+    transform, copy out, synchronise)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    M, N = len(x), len(y)
+    if out is None:
+        out = np.empty(M, dtype=np.float64)
+    nbytes = plan.workspace_size(M, N, host=True)
+    ws = _workspace(workspace, torch.device("cuda", torch.cuda.current_device()), nbytes)
+    check(lib().fgt1d_execute_host(plan.handle, _ptr(x), M, _ptr(y), _ptr(alpha), N, _ptr(out),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)), "execute_host")
+    return out
+
+
+def sort_merged(x, y, workspace=None, stream=None):
+    """Stable sorted order of the merged points [y, x] (uint32 merged indices as int64)."""
+    _dev(x, "x"), _dev(y, "y")
+    M, N = x.numel(), y.numel()
+    b = ctypes.c_size_t()
+    check(lib().fgt1d_sort_workspace_size(M, N, ctypes.byref(b)), "sort_workspace_size")
+    ws = _workspace(workspace, x.device, b.value)
+    perm = torch.empty(M + N, dtype=torch.int32, device=x.device)
+    st = _stream_ptr(stream)
+    check(lib().fgt1d_sort_merged(ctypes.c_void_p(x.data_ptr()), M, ctypes.c_void_p(y.data_ptr()), N,
+                                  ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(), st),
+          "sort_merged")
+    check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "sort_merged (device)")
+    return perm.to(torch.int64) & 0xFFFFFFFF

@@ -1,0 +1,114 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol, and its
+host-side parts (the SOE generator of step a0, plan selection, argument checks and
+workspace sizing) behave, without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import soe_cf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1909_09825_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def declared_symbols():
+    src = ""
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", f)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgt1d_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_1909_09825_gb300 import _lib
+    assert set(_lib.SIGNATURES) == set(names)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 8, 10, 12, 14])
+def test_soe_generator_matches_oracle(L, n):
+    """The product's C++ CF generator and the oracle's numpy one are independent
+    implementations of the same construction: same E_n, same nodes (to the problem's
+    conditioning, which grows with n)."""
+    import paper_1909_09825_gb300 as fgt
+    tau, W, En = fgt.soe_cf(n)
+    ot, oW, oE = soe_cf.cf_soe(n)
+    assert abs(En / oE - 1) < (0.05 if n < 14 else 0.2)
+    tol = {2: 1e-12, 4: 1e-12, 6: 1e-10, 8: 1e-9, 10: 1e-7, 12: 1e-5, 14: 2e-3}[n]
+    assert np.max(np.abs(W - oW)) / np.max(np.abs(oW)) < tol
+    assert np.max(np.abs(tau - ot)) / np.max(np.abs(ot)) < tol
+    assert np.all(tau.real > 0) and np.all(tau.imag > 0)
+    # the product's E_n claim holds on an independent grid
+    x = np.concatenate([[0.0], np.linspace(0, 15, 300001)])
+    assert np.max(np.abs(np.exp(-x * x / 4) - soe_cf.soe_eval(tau, W, x))) <= En * 1.01
+
+
+@pytest.mark.parametrize("eps", [0.1, 1e-3, 1e-6, 1e-8, 1e-10, 5e-12])
+def test_plan_picks_smallest_n(L, eps):
+    import paper_1909_09825_gb300 as fgt
+    p = fgt.Plan(0.37, eps)
+    assert p.E_n <= eps
+    assert p.n == 2 or fgt.soe_cf(p.n - 2)[2] > eps
+    assert p.n_e == p.n // 2 and abs(p.delta - 0.37) == 0
+
+
+def test_plan_errors(L):
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    for args in [(0.0, 1e-6), (-1.0, 1e-6), (float("nan"), 1e-6), (float("inf"), 1e-6), (1.0, 0.0), (1.0, 0.7)]:
+        with pytest.raises(_lib.FGTError) as e:
+            fgt.Plan(*args)
+        assert e.value.code == _lib.FGT1D_EINVAL
+    with pytest.raises(_lib.FGTError) as e:
+        fgt.Plan(1.0, 1e-14)
+    assert e.value.code == _lib.FGT1D_EUNSUPPORTED
+    with pytest.raises(_lib.FGTError) as e:
+        fgt.Plan(1.0, 1e-8, precision="fp32")
+    assert e.value.code == _lib.FGT1D_EUNSUPPORTED
+    with pytest.raises(_lib.FGTError) as e:
+        fgt.Plan(1.0, soe=([-1.0 + 1j], [1.0]))
+    assert e.value.code == _lib.FGT1D_EINVAL
+    assert L.fgt1d_plan_create(ctypes.c_double(1.0), ctypes.c_double(1e-6), 0, None) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_plan_create(ctypes.c_double(1.0), ctypes.c_double(1e-6), 8, ctypes.byref(ctypes.c_void_p())) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_soe_cf(7, *([None] * 6)) == _lib.FGT1D_EINVAL
+
+
+def test_workspace_size_and_bounds(L):
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    p = fgt.Plan(1e-3, 1e-6)
+    a, b = p.workspace_size(1000, 1000), p.workspace_size(1 << 20, 1 << 20)
+    assert 0 < a < b
+    assert p.workspace_size(1 << 20, 1 << 20, host=True) >= b + 4 * 8 * (1 << 20)
+    sz = ctypes.c_size_t()
+    assert L.fgt1d_workspace_size(p.handle, -1, 5, ctypes.byref(sz)) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_workspace_size(p.handle, 1 << 30, 1 << 30, ctypes.byref(sz)) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_workspace_size(p.handle, (1 << 30) - 1, 1 << 30, ctypes.byref(sz)) == _lib.FGT1D_OK
+    # execute rejects a missing or short workspace before touching the device
+    x = (ctypes.c_double * 4)()
+    assert L.fgt1d_execute(p.handle, x, 4, x, x, 4, x, None, 0, None) == _lib.FGT1D_EWORKSPACE
+    assert L.fgt1d_execute(p.handle, None, 4, x, x, 4, x, None, 0, None) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_strerror(3).decode().startswith("a coordinate")
+
+
+def test_product_imports_no_oracle():
+    """The product package never reaches into the oracle."""
+    pkg = os.path.join(ROOT, "paper_1909_09825_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle|#include.*oracle|liboracle", txt, re.M), f

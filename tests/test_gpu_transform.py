@@ -1,0 +1,181 @@
+"""GPU parity of the full transform (sort + sweeps + evaluate + unpermute) against
+the CPU oracle, through the C ABI.
+
+Tolerances
+- vs O1 (direct Gauss sum): ||u - u_ref||_inf / sum|alpha| <= 2 eps + 1e-13 (FP64 path)
+  and <= 2 eps + 5e-6 (FP32 path).  E_n <= eps bounds the SOE error (eq. 3.1), the
+  rest is rounding.
+- vs O3 (the paper's recurrence with the SAME SOE, so only rounding differs):
+  ||u - u_O3||_inf / sum|alpha| <= TOL_ARITH64 = 1e-12 (FP64).  Both sides lose at most
+  a few ulp per multiplier product; the GPU's products are at most R + 2 log2(P) deep,
+  the oracle's sequential chain up to P deep, so at P <= 1e5 the bound is
+  ~ P * 2^-53 ~ 1e-11 coherent and ~ sqrt(P) 2^-53 typical; 1e-12 leaves a margin of
+  about 30 over the typical case and is checked here on every case.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1909_09825_gb300 as fgt
+from oracle import oracle, soe_cf
+from paper_1909_09825_gb300 import inputs
+
+from gpu_util import gpu_transform, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL_ARITH64 = 1e-12
+
+
+def oracle_soe_plan(delta, eps, precision="fp64"):
+    n, tau, W, En = soe_cf.plan_soe(eps)
+    return fgt.Plan(delta, soe=(tau, W), precision=precision), tau, W
+
+
+def test_small_config_vs_direct(cuda):
+    """M = N = 1000, uniform, alpha ~ N(0,1), delta = 1e-3, eps = 1e-6, seed 0."""
+    x, y, a = inputs.uniform(1000, 1000, seed=0)
+    plan = fgt.Plan(1e-3, 1e-6)
+    assert plan.E_n <= 1e-6
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.direct(x, y, a, 1e-3)
+    assert rel_inf(u, ref, a) <= 2e-6 + 1e-13
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (1, 5), (7, 1), (33, 65), (1000, 1000), (2047, 1), (1, 2047),
+                                 (2048, 2048), (2049, 2047), (4097, 3000), (12345, 6789), (30001, 29999)])
+def test_ragged_vs_recurrence(cuda, M, N):
+    x, y, a = inputs.uniform(M, N, seed=M * 7 + N)
+    delta, eps = 1e-3, 1e-10
+    plan, tau, W = oracle_soe_plan(delta, eps)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-8, 1e-10])
+@pytest.mark.parametrize("delta", [1e-2, 1e-5])
+def test_eps_delta_vs_direct(cuda, eps, delta):
+    x, y, a = inputs.uniform(3000, 2500, seed=11)
+    plan = fgt.Plan(delta, eps)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.direct(x, y, a, delta)
+    assert rel_inf(u, ref, a) <= 2 * eps + 1e-13
+
+
+def test_ties_and_signed_zeros(cuda):
+    x, y, a = inputs.with_ties(5000, 4000, seed=3, n_distinct=50)
+    delta = 1e-2
+    plan, tau, W = oracle_soe_plan(delta, 1e-10)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+
+
+def test_all_points_identical(cuda):
+    x = np.full(3000, 0.25)
+    y = np.full(2000, 0.25)
+    a = np.random.default_rng(1).standard_normal(2000)
+    plan, tau, W = oracle_soe_plan(1e-3, 1e-8)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, 1e-3, tau, W)
+    # coincident pairs get S_n(0) = Re sum W_k (Fig. 4.2 code: weight of an identical source)
+    assert np.allclose(ref, np.sum(a) * np.sum(W.real), rtol=0, atol=1e-12 * np.abs(a).sum())
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+
+
+def test_mixture_vs_recurrence(cuda):
+    x, y, a = inputs.mixture(20000, 20000, seed=5)
+    delta = 1e-4
+    plan, tau, W = oracle_soe_plan(delta, 1e-10)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+
+
+@pytest.mark.parametrize("delta", [1e-7, 1e-4, 1e-1, 1e2, 1e4])
+def test_delta_sweep_vs_direct(cuda, delta):
+    """Fig. 5.2: accuracy over delta = 1e-7..1e4 stays within E_n."""
+    x, y, a = inputs.uniform(2000, 2000, seed=21, alpha="pos")
+    eps = 1e-8
+    plan = fgt.Plan(delta, eps)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.direct(x, y, a, delta)
+    assert rel_inf(u, ref, a) <= 2 * eps + 1e-13
+
+
+def test_hyperbolic_soe_vs_soe_direct(cuda):
+    """Any SOE runs through the same kernels: the hyperbolic-contour SOE of Sec. 3.4."""
+    tau, W, En = soe_cf.hyperbolic_soe(16)
+    x, y, a = inputs.uniform(3000, 3000, seed=8)
+    delta = 1e-3
+    plan = fgt.Plan(delta, soe=(tau, W))
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.soe_direct(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_fp32_path_vs_direct(cuda, eps):
+    x, y, a = inputs.uniform(20000, 20000, seed=13)
+    delta = 1e-4
+    plan = fgt.Plan(delta, eps, precision="fp32")
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.direct(x, y, a, delta, nthreads=0)
+    assert rel_inf(u, ref, a) <= 2 * eps + 5e-6
+
+
+def test_fp32_mixture_vs_direct(cuda):
+    x, y, a = inputs.mixture(40000, 40000, seed=2)
+    delta, eps = 1e-4, 1e-6
+    plan = fgt.Plan(delta, eps, precision="fp32")
+    u = gpu_transform(plan, x, y, a)
+    idx = np.random.default_rng(0).choice(len(x), 300, replace=False)
+    ref = oracle.direct(x[idx], y, a, delta)
+    assert rel_inf(u[idx], ref, a) <= 2 * eps + 5e-6
+
+
+def test_empty_inputs(cuda):
+    plan = fgt.Plan(1e-3, 1e-6)
+    d = cuda
+    x = torch.rand(10, dtype=torch.float64, device=d)
+    e = torch.empty(0, dtype=torch.float64, device=d)
+    u = fgt.transform(plan, x, e, e)
+    assert torch.all(u == 0)
+    u = fgt.transform(plan, e, x, torch.ones_like(x))
+    assert u.numel() == 0
+
+
+def test_nonfinite_coordinate_reported(cuda):
+    plan = fgt.Plan(1e-3, 1e-6)
+    x, y, a = inputs.uniform(100, 100, seed=1)
+    x[17] = np.nan
+    with pytest.raises(fgt._lib.FGTError) as ei:
+        gpu_transform(plan, x, y, a)
+    assert ei.value.code == fgt._lib.FGT1D_ENONFINITE
+    y[3] = np.inf
+    x[17] = 0.5
+    with pytest.raises(fgt._lib.FGTError) as ei:
+        gpu_transform(plan, x, y, a)
+    assert ei.value.code == fgt._lib.FGT1D_ENONFINITE
+    # the workspace status is cleared: a clean call succeeds afterwards
+    y[3] = 0.5
+    gpu_transform(plan, x, y, a)
+
+
+def test_execute_host_matches_device(cuda):
+    x, y, a = inputs.uniform(5000, 4000, seed=4)
+    plan = fgt.Plan(1e-3, 1e-6)
+    u_dev = gpu_transform(plan, x, y, a)
+    u_host = fgt.execute_host(plan, x, y, a)
+    assert np.array_equal(u_dev, u_host)
+
+
+def test_repeat_runs_agree(cuda):
+    """The decoupled look-back adds a timing-dependent set of predecessor aggregates,
+    so repeated runs may differ in rounding only (never by more than TOL_ARITH64)."""
+    x, y, a = inputs.uniform(50000, 50000, seed=6)
+    plan = fgt.Plan(1e-4, 1e-10)
+    u1 = gpu_transform(plan, x, y, a)
+    u2 = gpu_transform(plan, x, y, a)
+    assert rel_inf(u1, u2, a) <= TOL_ARITH64

@@ -1,0 +1,311 @@
+"""Benchmark of the GB300 SOE fast Gauss transform.
+
+One step = one full transform (merged sort, forward and backward SOE sweeps,
+evaluation, unpermutation) of M = N = 2^26 points uniform on [0, 1] with
+alpha ~ N(0, 1), inputs already resident in HBM (3.2 GB, larger than L2).  The
+headline is the FP64 path at eps = 1e-6, delta = 1e-5; the other (eps, delta,
+precision) combinations of the same workload are reported under "also".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica of the workload on its GPU (the
+single transform has no partition without an exchange step), the timed region is
+bracketed by barriers and rank 0 prints one JSON line with the max over ranks.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(M+N) points/s at eps=1e-6 and 1e-10 on 1 GB300; % of SFU/FP64/HBM roofline"
+LOG2_M = 26
+HEAD = dict(delta=1e-5, eps=1e-6, precision="fp64")
+ALSO = [dict(delta=1e-5, eps=1e-10, precision="fp64"), dict(delta=1e-2, eps=1e-6, precision="fp64"),
+        dict(delta=1e-2, eps=1e-10, precision="fp64"), dict(delta=1e-5, eps=1e-3, precision="fp64"),
+        dict(delta=1e-5, eps=1e-6, precision="fp32"), dict(delta=1e-2, eps=1e-6, precision="fp32")]
+# FP64 pipe peak: 152 SMs x 2 DFMA/clk/SM (measured by a DFMA throughput probe on this
+# GB300 pool) x 2 flop x 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Algorithmic FP64 pipe ops of the forward sweep kernel per (merged point, term): the
+# multiplier exp(-tau theta) as a degree-4 Taylor polynomial (C_ce = 8), one complex
+# multiply-add of the recurrence (4) and the evaluation at targets (2 per target, half
+# of the points); plus 2 per point (difference and scaling of the gap).
+C_CE = 8
+KERNELS_PER_TRANSFORM = 12   # histogram, pass plan, 8 radix passes, forward and backward sweeps
+WORKLOAD = ("plain FP64 at scale: M=N=2^26, x,y ~ U[0,1), alpha ~ N(0,1), delta=%g, eps=%g, unsorted "
+            "inputs (sort timed), seed 0")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(delta, eps, log2=21):
+    """The oracle's sorted-recurrence algorithm (the paper's, single thread) on a bounded
+    sample of the same workload."""
+    from oracle import oracle, soe_cf
+    from paper_1909_09825_gb300 import inputs
+    n, tau, W, En = soe_cf.plan_soe(eps)
+    M = 1 << log2
+    x, y, a = inputs.uniform(M, M, seed=0)
+    t0 = time.perf_counter()
+    oracle.recurrence(x, y, a, delta, tau, W)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * M / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": "M=N=2^%d of the same distribution, delta=%g, eps=%g (n_e=%d); stable merge sort + "
+                      "forward/backward recurrences, one thread, %.1f s" % (log2, delta, eps, len(tau), dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    delta, eps = HEAD["delta"], HEAD["eps"]
+    from oracle import oracle, soe_cf
+    from paper_1909_09825_gb300 import inputs
+    n, tau, W, En = soe_cf.plan_soe(eps)
+    log2 = 19
+    M = 1 << log2
+    x, y, a = inputs.uniform(M, M, seed=0)
+    for _ in range(args.warmup):
+        oracle.recurrence(x, y, a, delta, tau, W)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.recurrence(x, y, a, delta, tau, W)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = 2 * M / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD % (delta, eps), "M": 1 << LOG2_M, "N": 1 << LOG2_M,
+                       "delta": delta, "eps": eps},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: M=N=2^%d of the workload's distribution through the oracle's "
+                                       "sort + recurrences, one host thread" % log2},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2", type=int, default=LOG2_M, help="log2 of M = N (default 26)")
+    ap.add_argument("--no-also", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib, inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    M = N = 1 << args.log2
+    P = M + N
+    x, y, a = inputs.uniform(M, N, seed=0)
+    X, Y, A = (torch.from_numpy(v).to(dev) for v in (x, y, a))
+    U = torch.empty(M, dtype=torch.float64, device=dev)
+    ws = fgt.Workspace(dev)
+
+    def timed(cfg, steps, warmup, profile=False):
+        plan = fgt.Plan(cfg["delta"], cfg["eps"], precision=cfg["precision"])
+        buf = ws.get(plan.workspace_size(M, N))
+        for _ in range(warmup):
+            fgt.transform(plan, X, Y, A, out=U, workspace=ws)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * steps)]
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for s in range(steps):
+            if profile:
+                e4 = ev[4 * s: 4 * s + 4]
+                for e in e4:
+                    e.record(stream)      # creates the event; re-recorded inside the call
+                arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in e4])
+                _lib.check(_lib.lib().fgt1d_execute_profiled(
+                    plan.handle, ctypes.c_void_p(X.data_ptr()), M, ctypes.c_void_p(Y.data_ptr()),
+                    ctypes.c_void_p(A.data_ptr()), N, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
+                    buf.numel(), ctypes.c_void_p(stream.cuda_stream), arr), "execute_profiled")
+            else:
+                fgt.transform(plan, X, Y, A, out=U, workspace=ws, sync_check=False)
+        t_end.record(stream)
+        barrier()
+        _lib.check(_lib.lib().fgt1d_check(ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                          ctypes.c_void_p(stream.cuda_stream)), "bench (device status)")
+        ms = t_start.elapsed_time(t_end) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        stages = None
+        if profile:
+            st = np.array([[ev[4 * s + i].elapsed_time(ev[4 * s + i + 1]) for i in range(3)] for s in range(steps)])
+            stages = {"sort_ms": float(st[:, 0].mean()), "fwd_sweep_ms": float(st[:, 1].mean()),
+                      "bwd_sweep_ms": float(st[:, 2].mean())}
+        return plan, ms, stages
+
+    gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(gpu_uuid) as clk:
+        plan, ms, stages = timed(HEAD, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    value = world * P / (ms * 1e-3)
+
+    # roofline of the dominant kernel (forward sweep, FP64 pipe)
+    n_e = plan.n_e
+    fwd_ops = P * n_e * (C_CE + 4 + 2.0 * M / P) + 2 * P
+    fwd_s = stages["fwd_sweep_ms"] * 1e-3
+    achieved = 2 * fwd_ops / fwd_s / 1e12
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "k_sweep_fwd<double>", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "152 SMs x 2 DFMA/clk/SM (probe) x 2 flop x 2070 MHz",
+                "algorithmic_ops_per_unit": "unit = (merged point, SOE term); C_ce=%d + 4 + 2 M/P FP64 ops, "
+                                            "+2 per point" % C_CE,
+                "traffic": None}
+    traffic = _traffic_record(plan)
+    if traffic is not None:
+        roofline["traffic"] = traffic * P
+
+    also = []
+    if not args.no_also:
+        for cfg in ALSO:
+            p2, ms2, st2 = timed(cfg, 3, 2, profile=True)
+            also.append({"precision": cfg["precision"], "delta": cfg["delta"], "eps": cfg["eps"], "n_e": p2.n_e,
+                         "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2})
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    hx = torch.from_numpy(x).pin_memory().numpy()
+    hy = torch.from_numpy(y).pin_memory().numpy()
+    ha = torch.from_numpy(a).pin_memory().numpy()
+    hu = torch.empty(M, dtype=torch.float64).pin_memory().numpy()
+    hws = fgt.Workspace(dev)
+    fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
+    barrier()
+    e2e_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    del hws
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(HEAD["delta"], HEAD["eps"])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD % (HEAD["delta"], HEAD["eps"]), "M": M, "N": N,
+                           "delta": HEAD["delta"], "eps": HEAD["eps"], "n_e": plan.n_e, "E_n": plan.E_n,
+                           "precision": "fp64", "l2": "inputs (24 B/point, %.1f GB) larger than the 129 MB L2"
+                                                       % (24 * P / 2 ** 30 / 1.0),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "stages": stages, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": world * P / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 8 * (M + 2 * N),
+                        "d2h_bytes_per_step": 8 * M},
+                "gpu_launches": KERNELS_PER_TRANSFORM * args.steps, "clocks": clocks, "also": also}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _traffic_record(plan):
+    """DRAM bytes per merged point of the forward sweep from the committed ncu summary,
+    used only while the kernel source still matches the one that was profiled."""
+    import hashlib
+    f = os.path.join(ROOT, "profiles", "sweep_fwd_f64_traffic.json")
+    if not os.path.exists(f):
+        return None
+    rec = json.load(open(f))
+    src = os.path.join(ROOT, "paper_1909_09825_gb300", "csrc", "sweep.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h or rec.get("n_e") != plan.n_e:
+        return None
+    return rec["dram_bytes_per_point"]
+
+
+if __name__ == "__main__":
+    main()

@@ -110,6 +110,14 @@ int fgt1d_execute(fgt1d_plan plan, const double* x, int64_t M, const double* y,
                   const double* alpha, int64_t N, double* u, void* workspace, size_t ws_bytes,
                   fgt1d_stream stream);
 
+/* fgt1d_execute that also records four caller-created CUDA events (cudaEvent_t,
+ * any may be NULL) on `stream`: events[0] before the sort, events[1] after the sort,
+ * events[2] after the forward sweep kernel, events[3] after the backward sweep kernel.
+ * Used to time each stage on the launching stream. */
+int fgt1d_execute_profiled(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                           const double* alpha, int64_t N, double* u, void* workspace, size_t ws_bytes,
+                           fgt1d_stream stream, void* const* events);
+
 /* Same transform for HOST arrays (pageable or pinned): copies x, y, alpha to the
  * device, runs fgt1d_execute, copies u back and synchronises the stream.  The
  * workspace (device) must hold fgt1d_workspace_size_host bytes; it also carries the

@@ -141,13 +141,16 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
 
 int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
-                  double* u, char* ws, const Layout& L, cudaStream_t st) {
+                  double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* ev = nullptr) {
+    auto rec = [&](int i) { return (ev && ev[i]) ? cudaEventRecord(ev[i], st) : cudaSuccess; };
     if (M == 0) return FGT1D_OK;
     if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
-    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, st);
+    cudaError_t e = rec(0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SortArgs sa = sort_args(x, M, y, N, ws, L);
     e = launch_sort(sa, st);
+    if (e == cudaSuccess) e = rec(1);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w;
     w.P = M + N;
@@ -167,7 +170,9 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
     w.status = sa.status;
     w.tiles = L.sweep_tiles;
     SweepConsts c = make_consts(p);
-    e = (p.flags & FGT1D_FP32) ? launch_sweeps_f32(w, c, st) : launch_sweeps_f64(w, c, st);
+    cudaEvent_t mid = ev ? ev[2] : nullptr;
+    e = (p.flags & FGT1D_FP32) ? launch_sweeps_f32(w, c, st, mid) : launch_sweeps_f64(w, c, st, mid);
+    if (e == cudaSuccess) e = rec(3);
     return cuda_status(e);
 }
 
@@ -206,6 +211,21 @@ extern "C" int fgt1d_execute(fgt1d_plan plan, const double* x, int64_t M, const 
     }
     return run_transform(*plan, x, M, y, alpha, N, u, static_cast<char*>(workspace), L,
                          static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fgt1d_execute_profiled(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                                      const double* alpha, int64_t N, double* u, void* workspace, size_t ws_bytes,
+                                      fgt1d_stream stream, void* const* events) {
+    if (!plan || !sizes_ok(M, N) || !events) return FGT1D_EINVAL;
+    if (M > 0 && (!x || !u)) return FGT1D_EINVAL;
+    if (N > 0 && M > 0 && (!y || !alpha)) return FGT1D_EINVAL;
+    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false);
+    if (M > 0 && N > 0) {
+        int r = ws_ok(workspace, ws_bytes, L);
+        if (r) return r;
+    }
+    return run_transform(*plan, x, M, y, alpha, N, u, static_cast<char*>(workspace), L,
+                         static_cast<cudaStream_t>(stream), reinterpret_cast<cudaEvent_t const*>(events));
 }
 
 extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,

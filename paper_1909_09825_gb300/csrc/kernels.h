@@ -71,8 +71,9 @@ struct SweepArgs {
 
 int sweep_tile_f64();  // points per sweep tile
 int sweep_tile_f32();
-cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
-cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
+// `mid` (may be null) is recorded on st between the forward and the backward kernel.
+cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
+cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
 
 // copies the sorted merged indices (final sort buffer) to perm
 cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st);

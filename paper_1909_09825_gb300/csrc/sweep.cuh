@@ -207,19 +207,104 @@ static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile
     }
 }
 
+// Shared-memory footprint of the sweep kernels: coordinates (double), strengths (Real)
+// and the per-term exclusive thread prefixes (Real), padded one slot per R points so
+// that a warp reading one point per thread (stride R) hits distinct banks.
+template <typename Real, int NE, int T, int R>
+struct SweepSmem {
+    static constexpr int TILE = T * R;
+    static constexpr int TP = TILE + TILE / R + 1;
+    static constexpr size_t z_off = 0;
+    static constexpr size_t al_off = z_off + sizeof(double) * TP;
+    static constexpr size_t scan_off = (al_off + sizeof(Real) * TP + 15) / 16 * 16;
+    static constexpr size_t bytes = scan_off + sizeof(Real) * 4 * NE * T;
+};
+
+template <int R>
+__device__ __forceinline__ int pad(int i) { return i + i / R; }
+
+// Per-term combine of the warp totals, look-back and publication (one lane per term).
+// dir = -1: forward (anchor = last point, carry comes from lower tiles);
+// dir = +1: backward (anchor = first point, carry comes from higher tiles).
+// s_w[k][w] holds each warp's total map (M, F) in the sweep direction; on return
+// s_win[k][w] holds the state entering warp w (after the carry).
+template <int NE, int NW>
+__device__ __forceinline__ void tile_combine(const SweepArgs& a, const SweepConsts& c, TileDesc* desc, int64_t tile,
+                                             int dir, bool first_in_dir, double zanchor, double zref,
+                                             double (*s_w)[NW][4], double (*s_win)[NW][2], int k) {
+    double pre[NW][4];
+    double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int ww = dir < 0 ? q : NW - 1 - q;  // sweep order
+        pre[ww][0] = Pr; pre[ww][1] = Pi; pre[ww][2] = Qr; pre[ww][3] = Qi;
+        cfma<double>(s_w[k][ww][0], s_w[k][ww][1], Qr, Qi, s_w[k][ww][2], s_w[k][ww][3], Qr, Qi);
+        cmul<double>(s_w[k][ww][0], s_w[k][ww][1], Pr, Pi, Pr, Pi);
+    }
+    TileDesc* dd = desc + tile * NE + k;
+    double Cr = 0, Ci = 0;
+    const double tr = c.tau_re[k], ti = c.tau_im[k], s = c.s;
+    if (first_in_dir) {
+        publish_inc(dd, Qr, Qi, Qr, Qi, zanchor, true);
+    } else {
+        publish_agg(dd, Qr, Qi, zanchor);
+        look_back(desc, tile, dir, a.tiles, NE, k, tr, ti, s, zref, Cr, Ci, a.status);
+        double Er, Ei;
+        cexp_neg(tr, ti, s * fabs(zanchor - zref), Er, Ei);
+        double Ir, Ii;
+        cfma<double>(Er, Ei, Cr, Ci, Qr, Qi, Ir, Ii);
+        publish_inc(dd, 0, 0, Ir, Ii, zanchor, false);
+    }
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+        double xr, xi;
+        cfma<double>(pre[ww][0], pre[ww][1], Cr, Ci, pre[ww][2], pre[ww][3], xr, xi);
+        s_win[k][ww][0] = xr;
+        s_win[k][ww][1] = xi;
+    }
+}
+
+// Stages the tile: coordinates, strengths (0 at targets) and target bits.  Points past
+// the end get z = 0, alpha = 0 and are not targets; n_extra points after the tile
+// (the next tile's first point for the backward sweep) are loaded as coordinates only.
+template <typename Real, int T, int R>
+__device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* __restrict__ keys,
+                                           const uint32_t* __restrict__ vals, int64_t base, int nvalid,
+                                           double* s_z, Real* s_al, uint32_t* s_tgt) {
+    constexpr int TILE = T * R;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < TILE; i += T) {
+        double z = 0.0, al = 0.0;
+        bool tg = false;
+        if (i < nvalid) {
+            const int64_t p = base + i;
+            z = key_coord(keys[p]);
+            const uint32_t v = vals[p];
+            if ((int64_t)v < a.N) al = __ldg(&a.alpha[v]);
+            else tg = true;
+        }
+        s_z[pad<R>(i)] = z;
+        s_al[pad<R>(i)] = (Real)al;
+        const unsigned b = __ballot_sync(0xffffffffu, tg);
+        if (lane == 0) s_tgt[i >> 5] = b;
+    }
+}
+
 template <typename Real, int NE, int T, int R>
 __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepConsts c) {
+    using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = sizeof(Real) == 8;
-    extern __shared__ __align__(16) double s_dyn[];
-    double* s_al = s_dyn;          // [TILE] strengths (0 at targets)
-    double* s_acc = s_dyn + TILE;  // [TILE] coordinates, then Re sum_k W_k F_k
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
+    Real* s_al = reinterpret_cast<Real*>(smem + SM::al_off);
+    Real* s_scan = reinterpret_cast<Real*>(smem + SM::scan_off);  // [NE][4][T]
+    __shared__ double s_w[NE][NW][4];
+    __shared__ double s_win[NE][NW][2];
     __shared__ uint32_t s_tgt[TILE / 32];
-    __shared__ double s_w[NW][4];
-    __shared__ double s_win[NW][2];
     __shared__ uint32_t s_tile;
-    __shared__ double s_zprev, s_zend;
+    __shared__ double s_zprev;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(&a.tile_ctr[0], 1u);
@@ -230,27 +315,14 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
-
-    // stage coordinates (in s_acc), strengths and target flags
-    for (int i = tid; i < TILE; i += T) {
-        const int64_t p = base + i;
-        double z = 0.0, al = 0.0;
-        bool tg = false;
-        if (i < nvalid) {
-            z = key_coord(keys[p]);
-            const uint32_t v = vals[p];
-            if ((int64_t)v < a.N) al = __ldg(&a.alpha[v]);
-            else tg = true;
-        }
-        s_acc[i] = z;
-        s_al[i] = al;
-        const unsigned b = __ballot_sync(0xffffffffu, tg);
-        if (lane == 0) s_tgt[i >> 5] = b;
-    }
+    stage_tile<Real, T, R>(a, keys, vals, base, nvalid, s_z, s_al, s_tgt);
     if (tid == 0) s_zprev = base > 0 ? key_coord(keys[base - 1]) : 0.0;
     __syncthreads();
+
+    // my R points: gaps theta = s (z_i - z_{i-1}) (FP64 difference), target bits
     const double s = c.s;
     const int i0 = tid * R;
+    const double zprev = s_zprev;
     Real th[R];
     uint32_t thw[R];
     uint32_t hw = 0;
@@ -258,42 +330,41 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r;
         double t = 0.0;
-        if (i < nvalid && base + i > 0) t = s * (s_acc[i] - (i > 0 ? s_acc[i - 1] : s_zprev));
+        if (i < nvalid && base + i > 0) t = s * (s_z[pad<R>(i)] - (i > 0 ? s_z[pad<R>(i - 1)] : zprev));
         th[r] = (Real)t;
         thw[r] = theta_hw<Real>(th[r]);
         hw = max(hw, thw[r]);
     }
-    if (tid == 0) s_zend = s_acc[nvalid - 1];
-    double th_span = 0.0;
-    if (i0 < nvalid && (base > 0 || i0 > 0)) {
-        const double zl = s_acc[min(i0 + R - 1, nvalid - 1)];
-        const double zf = i0 > 0 ? s_acc[i0 - 1] : s_zprev;
-        th_span = s * (zl - zf);
-    }
-    __syncthreads();
-    for (int i = tid; i < TILE; i += T) s_acc[i] = 0.0;
-    const double zprev = s_zprev, zend = s_zend;
     hw = __reduce_max_sync(0xffffffffu, hw);
+    double th_span = 0.0;
+    if (i0 < nvalid && (base > 0 || i0 > 0))
+        th_span = s * (s_z[pad<R>(min(i0 + R - 1, nvalid - 1))] - (i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev));
     const Real thsp = (Real)th_span;
     const uint32_t thsp_w = theta_hw<Real>(thsp);
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, thsp_w);
-    uint32_t tmask = 0;  // target bits of my R points
+    uint32_t tmask = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
+    const double zend = s_z[pad<R>(nvalid - 1)];
 
+    // phase A: per term, thread aggregates and the warp scan
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
         const int deg = taylor_degree<Real>(c, k, hw);
         Real mr[R], mi[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
-        // thread aggregate with zero carry
-        Real fr = (Real)s_al[i0], fi = 0;
+        if constexpr (kF64) {
+            double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
 #pragma unroll
-        for (int r = 1; r < R; ++r) cfma<Real>(mr[r], mi[r], fr, fi, (Real)s_al[i0 + r], Real(0), fr, fi);
+            for (int r = 0; r < R; ++r)
+                if (i0 + r < nvalid) mt[r] = make_double2((double)mr[r], (double)mi[r]);
+        }
+        Real fr = s_al[pad<R>(i0)], fi = 0;
+#pragma unroll
+        for (int r = 1; r < R; ++r) cfma<Real>(mr[r], mi[r], fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
         Real Mr, Mi;
         multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, thsp_w, Mr, Mi);
-        // warp inclusive scan of (M, F)
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Real Mor = __shfl_up_sync(0xffffffffu, Mr, o), Moi = __shfl_up_sync(0xffffffffu, Mi, o);
@@ -306,78 +377,70 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         Real Mxr = __shfl_up_sync(0xffffffffu, Mr, 1), Mxi = __shfl_up_sync(0xffffffffu, Mi, 1);
         Real Fxr = __shfl_up_sync(0xffffffffu, fr, 1), Fxi = __shfl_up_sync(0xffffffffu, fi, 1);
         if (lane == 0) { Mxr = 1; Mxi = 0; Fxr = 0; Fxi = 0; }
+        Real* sc = s_scan + (size_t)k * 4 * T;
+        sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 31) {
-            s_w[w][0] = (double)Mr; s_w[w][1] = (double)Mi;
-            s_w[w][2] = (double)fr; s_w[w][3] = (double)fi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double pre[NW][4];
-            double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
-#pragma unroll
-            for (int ww = 0; ww < NW; ++ww) {
-                pre[ww][0] = Pr; pre[ww][1] = Pi; pre[ww][2] = Qr; pre[ww][3] = Qi;
-                cfma<double>(s_w[ww][0], s_w[ww][1], Qr, Qi, s_w[ww][2], s_w[ww][3], Qr, Qi);
-                cmul<double>(s_w[ww][0], s_w[ww][1], Pr, Pi, Pr, Pi);
-            }
-            TileDesc* dd = a.fdesc + tile * NE + k;
-            double Cr = 0, Ci = 0;
-            const double tr = c.tau_re[k], ti = c.tau_im[k];
-            if (tile == 0) {
-                publish_inc(dd, Qr, Qi, Qr, Qi, zend, true);
-            } else {
-                publish_agg(dd, Qr, Qi, zend);
-                look_back(a.fdesc, tile, -1, a.tiles, NE, k, tr, ti, s, zprev, Cr, Ci, a.status);
-                double Er, Ei;
-                cexp_neg(tr, ti, s * (zend - zprev), Er, Ei);
-                double Ir, Ii;
-                cfma<double>(Er, Ei, Cr, Ci, Qr, Qi, Ir, Ii);
-                publish_inc(dd, 0, 0, Ir, Ii, zend, false);
-            }
-#pragma unroll
-            for (int ww = 0; ww < NW; ++ww) {
-                double xr, xi;
-                cfma<double>(pre[ww][0], pre[ww][1], Cr, Ci, pre[ww][2], pre[ww][3], xr, xi);
-                s_win[ww][0] = xr;
-                s_win[ww][1] = xi;
-            }
-        }
-        __syncthreads();
-        Real Sr, Si;
-        cfma<Real>(Mxr, Mxi, (Real)s_win[w][0], (Real)s_win[w][1], Fxr, Fxi, Sr, Si);
-        // final pass
-        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        fr = Sr;
-        fi = Si;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            cfma<Real>(mr[r], mi[r], fr, fi, (Real)s_al[i0 + r], Real(0), fr, fi);
-            if ((tmask >> r) & 1u) s_acc[i0 + r] += (double)fma(Wr, fr, -Wi * fi);
-        }
-        if constexpr (kF64) {
-            double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (i0 + r < nvalid) mt[r] = make_double2((double)mr[r], (double)mi[r]);
+            s_w[k][w][0] = (double)Mr; s_w[k][w][1] = (double)Mi;
+            s_w[k][w][2] = (double)fr; s_w[k][w][3] = (double)fi;
         }
     }
     __syncthreads();
-    for (int i = tid; i < nvalid; i += T) a.fwd[base + i] = s_acc[i];
+    // phase B: one lane per term joins the warps and the tiles
+    if (tid < NE) tile_combine<NE, NW>(a, c, a.fdesc, tile, -1, tile == 0, zend, zprev, s_w, s_win, tid);
+    __syncthreads();
+    // phase C: apply the carries, final pass, evaluation at targets
+    Real acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 1
+    for (int k = 0; k < NE; ++k) {
+        const Real* sc = s_scan + (size_t)k * 4 * T;
+        Real fr, fi;
+        cfma<Real>(sc[tid], sc[T + tid], (Real)s_win[k][w][0], (Real)s_win[k][w][1], sc[2 * T + tid],
+                   sc[3 * T + tid], fr, fi);
+        Real mr[R], mi[R];
+        if constexpr (kF64) {
+            const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
+                mr[r] = (Real)m.x;
+                mi[r] = (Real)m.y;
+            }
+        } else {
+            const int deg = taylor_degree<Real>(c, k, hw);
+#pragma unroll
+            for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
+        }
+        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cfma<Real>(mr[r], mi[r], fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+            if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+        }
+    }
+    // forward partial sums, written coalesced through shared memory
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = (double)acc[r];
+    __syncthreads();
+    for (int i = tid; i < nvalid; i += T) a.fwd[base + i] = s_z[pad<R>(i)];
 }
 
 template <typename Real, int NE, int T, int R>
 __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepConsts c) {
+    using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = sizeof(Real) == 8;
-    extern __shared__ __align__(16) double s_dyn[];
-    double* s_al = s_dyn;          // [TILE]
-    double* s_acc = s_dyn + TILE;  // [TILE + 1] coordinates, then Re sum_k W_k B_k
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
+    Real* s_al = reinterpret_cast<Real*>(smem + SM::al_off);
+    Real* s_scan = reinterpret_cast<Real*>(smem + SM::scan_off);
+    __shared__ double s_w[NE][NW][4];
+    __shared__ double s_win[NE][NW][2];
     __shared__ uint32_t s_tgt[TILE / 32];
-    __shared__ double s_w[NW][4];
-    __shared__ double s_win[NW][2];
     __shared__ uint32_t s_tile;
-    __shared__ double s_znext, s_zfirst;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(&a.tile_ctr[1], 1u);
@@ -389,37 +452,14 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
-
-    for (int i = tid; i < TILE; i += T) {
-        const int64_t p = base + i;
-        double z = 0.0, al = 0.0;
-        bool tg = false;
-        if (i < nvalid) {
-            z = key_coord(keys[p]);
-            const uint32_t v = vals[p];
-            if ((int64_t)v < a.N) al = __ldg(&a.alpha[v]);
-            else tg = true;
-        }
-        s_acc[i] = z;
-        s_al[i] = al;
-        const unsigned b = __ballot_sync(0xffffffffu, tg);
-        if (lane == 0) s_tgt[i >> 5] = b;
-    }
-    if (tid == 0) {
-        s_znext = has_next ? key_coord(keys[base + TILE]) : 0.0;
-        s_acc[TILE] = s_znext;
-    }
+    stage_tile<Real, T, R>(a, keys, vals, base, nvalid, s_z, s_al, s_tgt);
+    if (tid == 0) s_z[pad<R>(TILE)] = has_next ? key_coord(keys[base + TILE]) : 0.0;
     __syncthreads();
+
     const double s = c.s;
-    if (tid == 0) s_zfirst = s_acc[0];
     const int i0 = tid * R;
-    double th_span = 0.0;
-    {
-        const int inext = i0 + R;  // first point of the next thread (or next tile)
-        const bool nxt = inext < nvalid || (inext == TILE && has_next);
-        if (i0 < nvalid && nxt) th_span = s * (s_acc[inext] - s_acc[i0]);
-    }
-    // th[r]: theta between points i0+r and i0+r+1 (FP32 path only; FP64 reads the table)
+    const double znext = s_z[pad<R>(TILE)], zfirst = s_z[0];
+    // th[r]: gap between points i0+r and i0+r+1 (the FP64 path reads the stored multipliers)
     Real th[R];
     uint32_t thw[R];
     uint32_t hw = 0;
@@ -428,16 +468,19 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         for (int r = 0; r < R; ++r) {
             const int i = i0 + r;
             double t = 0.0;
-            if (i + 1 < nvalid || (i + 1 == TILE && has_next)) t = s * (s_acc[i + 1] - s_acc[i]);
+            if (i + 1 < nvalid || (i + 1 == TILE && has_next)) t = s * (s_z[pad<R>(i + 1)] - s_z[pad<R>(i)]);
             th[r] = (Real)t;
             thw[r] = theta_hw<Real>(th[r]);
             hw = max(hw, thw[r]);
         }
         hw = __reduce_max_sync(0xffffffffu, hw);
     }
-    __syncthreads();
-    for (int i = tid; i < TILE; i += T) s_acc[i] = 0.0;
-    const double znext = s_znext, zfirst = s_zfirst;
+    double th_span = 0.0;
+    {
+        const int inext = i0 + R;
+        if (i0 < nvalid && (inext < nvalid || (inext == TILE && has_next)))
+            th_span = s * (s_z[pad<R>(inext)] - s_z[pad<R>(i0)]);
+    }
     const Real thsp = (Real)th_span;
     const uint32_t thsp_w = theta_hw<Real>(thsp);
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, thsp_w);
@@ -445,16 +488,13 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
 
-#pragma unroll 1
-    for (int k = 0; k < NE; ++k) {
-        // mm[r]: multiplier between point i0+r and i0+r+1
-        Real mr[R], mi[R];
+    auto load_mult = [&](int k, Real* mr, Real* mi) {
         if constexpr (kF64) {
             const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0 + 1;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int64_t p = base + i0 + r + 1;
-                double2 m = p < a.P ? __ldcs(&mt[r]) : make_double2(0.0, 0.0);
+                double2 m = p < a.P ? mt[r] : make_double2(0.0, 0.0);
                 mr[r] = (Real)m.x;
                 mi[r] = (Real)m.y;
             }
@@ -463,13 +503,17 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
 #pragma unroll
             for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
         }
-        // thread aggregate (state at my first point, zero carry from the right)
-        Real br = (Real)s_al[i0 + R - 1], bi = 0;
+    };
+
+#pragma unroll 1
+    for (int k = 0; k < NE; ++k) {
+        Real mr[R], mi[R];
+        load_mult(k, mr, mi);
+        Real br = s_al[pad<R>(i0 + R - 1)], bi = 0;
 #pragma unroll
-        for (int r = R - 2; r >= 0; --r) cfma<Real>(mr[r], mi[r], br, bi, (Real)s_al[i0 + r], Real(0), br, bi);
+        for (int r = R - 2; r >= 0; --r) cfma<Real>(mr[r], mi[r], br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
         Real Mr, Mi;
         multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, thsp_w, Mr, Mi);
-        // warp suffix scan
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Real Mor = __shfl_down_sync(0xffffffffu, Mr, o), Moi = __shfl_down_sync(0xffffffffu, Mi, o);
@@ -482,60 +526,43 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         Real Mxr = __shfl_down_sync(0xffffffffu, Mr, 1), Mxi = __shfl_down_sync(0xffffffffu, Mi, 1);
         Real Fxr = __shfl_down_sync(0xffffffffu, br, 1), Fxi = __shfl_down_sync(0xffffffffu, bi, 1);
         if (lane == 31) { Mxr = 1; Mxi = 0; Fxr = 0; Fxi = 0; }
+        Real* sc = s_scan + (size_t)k * 4 * T;
+        sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 0) {
-            s_w[w][0] = (double)Mr; s_w[w][1] = (double)Mi;
-            s_w[w][2] = (double)br; s_w[w][3] = (double)bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double post[NW][4];
-            double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
-#pragma unroll
-            for (int ww = NW - 1; ww >= 0; --ww) {
-                post[ww][0] = Pr; post[ww][1] = Pi; post[ww][2] = Qr; post[ww][3] = Qi;
-                cfma<double>(s_w[ww][0], s_w[ww][1], Qr, Qi, s_w[ww][2], s_w[ww][3], Qr, Qi);
-                cmul<double>(s_w[ww][0], s_w[ww][1], Pr, Pi, Pr, Pi);
-            }
-            TileDesc* dd = a.bdesc + tile * NE + k;
-            double Cr = 0, Ci = 0;
-            const double tr = c.tau_re[k], ti = c.tau_im[k];
-            if (!has_next) {
-                publish_inc(dd, Qr, Qi, Qr, Qi, zfirst, true);
-            } else {
-                publish_agg(dd, Qr, Qi, zfirst);
-                look_back(a.bdesc, tile, +1, a.tiles, NE, k, tr, ti, s, znext, Cr, Ci, a.status);
-                double Er, Ei;
-                cexp_neg(tr, ti, s * (znext - zfirst), Er, Ei);
-                double Ir, Ii;
-                cfma<double>(Er, Ei, Cr, Ci, Qr, Qi, Ir, Ii);
-                publish_inc(dd, 0, 0, Ir, Ii, zfirst, false);
-            }
-#pragma unroll
-            for (int ww = 0; ww < NW; ++ww) {
-                double xr, xi;
-                cfma<double>(post[ww][0], post[ww][1], Cr, Ci, post[ww][2], post[ww][3], xr, xi);
-                s_win[ww][0] = xr;
-                s_win[ww][1] = xi;
-            }
-        }
-        __syncthreads();
-        Real Sr, Si;  // state at the first point of the next thread
-        cfma<Real>(Mxr, Mxi, (Real)s_win[w][0], (Real)s_win[w][1], Fxr, Fxi, Sr, Si);
-        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        br = Sr;
-        bi = Si;
-#pragma unroll
-        for (int r = R - 1; r >= 0; --r) {
-            cfma<Real>(mr[r], mi[r], br, bi, (Real)s_al[i0 + r], Real(0), br, bi);
-            if ((tmask >> r) & 1u) s_acc[i0 + r] += (double)fma(Wr, br, -Wi * bi);
+            s_w[k][w][0] = (double)Mr; s_w[k][w][1] = (double)Mi;
+            s_w[k][w][2] = (double)br; s_w[k][w][3] = (double)bi;
         }
     }
+    __syncthreads();
+    if (tid < NE) tile_combine<NE, NW>(a, c, a.bdesc, tile, +1, !has_next, zfirst, znext, s_w, s_win, tid);
+    __syncthreads();
+    Real acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 1
+    for (int k = 0; k < NE; ++k) {
+        const Real* sc = s_scan + (size_t)k * 4 * T;
+        Real br, bi;  // state at the first point of the next thread
+        cfma<Real>(sc[tid], sc[T + tid], (Real)s_win[k][w][0], (Real)s_win[k][w][1], sc[2 * T + tid],
+                   sc[3 * T + tid], br, bi);
+        Real mr[R], mi[R];
+        load_mult(k, mr, mi);
+        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            cfma<Real>(mr[r], mi[r], br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+            if ((tmask >> r) & 1u) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = (double)acc[r];
     __syncthreads();
     for (int i = tid; i < nvalid; i += T) {
         if ((s_tgt[i >> 5] >> (i & 31)) & 1u) {
             const int64_t p = base + i;
             const uint32_t v = vals[p];
-            a.u[(int64_t)v - a.N] = a.fwd[p] + s_acc[i];
+            a.u[(int64_t)v - a.N] = a.fwd[p] + s_z[pad<R>(i)];
         }
     }
 }

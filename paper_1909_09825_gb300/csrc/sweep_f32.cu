@@ -8,7 +8,7 @@ constexpr int kT = 256, kR = 16;
 
 template <int NE>
 cudaError_t run(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {
-    const size_t smem = sizeof(double) * (2 * kT * kR + 1);
+    const size_t smem = SweepSmem<float, NE, kT, kR>::bytes;
     auto kf = k_sweep_fwd<float, NE, kT, kR>;
     auto kb = k_sweep_bwd<float, NE, kT, kR>;
     cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -92,7 +92,8 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
     std::memset(&c, 0, sizeof(c));
     c.n_e = p.n_e;
     c.s = 1.0 / std::sqrt(p.delta);
-    const double u64 = std::ldexp(1.0, -56), u32 = std::ldexp(1.0, -27);
+    c.s_f = (float)c.s;
+    const double u64 = std::ldexp(1.0, -53), u32 = std::ldexp(1.0, -26);
     for (int k = 0; k < p.n_e; ++k) {
         c.tau_re[k] = p.tau_re[k];
         c.tau_im[k] = p.tau_im[k];
@@ -112,9 +113,10 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
             ar = nr;
             ai = ni;
         }
-        // degree d is enough while (|tau| theta)^d / (d+1)! <= u: the truncation error of
-        // each multiplier stays below u times its first-order term, so it cannot
-        // accumulate past u times the total decay along a sweep.
+        // degree d is enough while (|tau| theta)^d / (d+1)! <= u (the unit roundoff): the
+        // truncation error of each multiplier stays below u times its first-order term
+        // |tau theta|, so along a sweep it cannot accumulate past u sum |tau theta|, i.e.
+        // u (|tau| / Re tau) times the decay length, a few tens of ulps.
         const double at = std::hypot(p.tau_re[k], p.tau_im[k]);
         double fact = 1.0;
         for (int d = 0; d <= kTaylorMax; ++d) {
@@ -162,7 +164,7 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
     w.plan = sa.plan;
     w.alpha = alpha;
     w.mult = L.mult ? reinterpret_cast<double2*>(ws + L.mult) : nullptr;
-    w.fwd = reinterpret_cast<double*>(ws + L.fwd);
+    w.fwd = ws + L.fwd;
     w.u = u;
     w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
     w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);

@@ -31,6 +31,7 @@ constexpr int kTaylorMax = 12;
 struct SweepConsts {
     int n_e;
     double s;                       // 1 / sqrt(delta)
+    float s_f;                      // the same in FP32
     double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
     double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
     // Taylor coefficients (-tau_k)^j / j!, j = 0..kTaylorMax, per term

@@ -44,9 +44,9 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
 
 // ---- sweeps (steps a3-a7) ----
 struct TileDesc {           // one (tile, term) entry of the decoupled look-back
-    double agg_re, agg_im;  // tile aggregate (zero carry)
+    double agg_re, agg_im;  // tile aggregate (zero carry) at the tile's anchor point
     double inc_re, inc_im;  // inclusive value (all carries)
-    double z;               // anchor coordinate (last point: forward; first point: backward)
+    double M_re, M_im;      // exp(-tau s (anchor - previous anchor)), computed directly
     uint32_t flag;          // 0 none, 1 aggregate, 2 inclusive
     uint32_t pad;
 };
@@ -60,7 +60,7 @@ struct SweepArgs {
     const SortPlan* plan;
     const double* alpha;
     double2* mult;          // [n_e][P] multiplier table (FP64 path) or nullptr
-    double* fwd;            // [P] forward partial sums Re sum_k W_k h+_k at targets
+    void* fwd;              // [P] forward partial sums Re sum_k W_k h+_k at targets (double; float on the FP32 path)
     double* u;              // [M] output
     TileDesc* fdesc;        // [tiles][n_e]
     TileDesc* bdesc;        // [tiles][n_e]

@@ -12,23 +12,28 @@
 // B every y_j > x_i (eq. 4.4).
 //
 // GB300 design.  Each recurrence is an associative scan of affine maps h -> m h + a.
-// A CTA owns a tile of T*R consecutive points; each thread runs R points sequentially
-// (work-efficient), a warp shuffle scan and a per-CTA combine join the threads, and a
-// decoupled look-back joins the tiles: each (tile, term) publishes its aggregate and
-// then its inclusive value, and a tile's carry is assembled from predecessors with
-// span multipliers exp(-tau s (z_a - z_b)) computed directly from the FP64 anchor
-// coordinates rather than as products, so no multiplier chain grows with the number
-// of tiles.  Terms are processed one at a time so that only one term's R multipliers
-// sit in registers.  Per-point multipliers use a Taylor polynomial of warp-uniform
-// degree chosen from the warp's largest gap (integer compares on the high word of
-// theta), falling back to exp/sincos for large gaps.
+// A CTA owns a tile of T*R consecutive points; each thread runs R consecutive points
+// sequentially (work-efficient), a warp shuffle scan joins the threads of a warp, and
+// one lane per term joins the warps and the tiles.  Per tile the kernel runs
+//   phase A  per term: multipliers, thread aggregates, warp scans (exclusive prefixes
+//            kept in shared memory);
+//   phase B  per term (one lane each): combine the warp totals, publish the tile
+//            aggregate with the tile's span multiplier exp(-tau s (z_anchor - z_prev))
+//            computed directly from the FP64 anchor coordinates, decoupled look-back
+//            over the neighbouring tiles (one complex multiply-add per predecessor,
+//            using the published span multipliers), publish the inclusive value;
+//   phase C  per term: apply the carries, final pass, evaluation at targets.
+// Per-point multipliers use a Taylor polynomial of warp-uniform degree chosen from
+// the warp's largest gap (integer compares on the bit pattern of theta), falling back
+// to exp/sincos for large gaps.
 //
-// FP64 path (Real = double): every step in FP64; the forward kernel stores the
-// multipliers (16 B per point and term) so the backward kernel does not recompute
-// them: on GB300 a DFMA costs 1/62 of an FFMA while a 32 B store+load is cheaper
-// than the eight or more DFMAs it replaces.
-// FP32 path (Real = float): multipliers and in-tile recurrences in FP32 complex from
-// FP64 coordinate differences; tile aggregates, carries and anchor multipliers in FP64.
+// FP64 path (Real = double): every step in FP64.  The forward kernel stores the
+// multipliers (16 B per point and term): on GB300 one DFMA costs as much issue time
+// as 62 FFMAs, and reloading 16 B is cheaper than the 6-10 DFMAs of a multiplier.
+// FP32 path (Real = float): gaps, multipliers and in-tile recurrences in FP32
+// complex; tile aggregates, span multipliers and carries in FP64.  Gaps come from the
+// integer difference of the sorted keys and FP64<->FP32 conversions are done with
+// integer bit operations, so the per-point work issues no FP64-pipe instruction.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,8 +58,58 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
     return v;
 }
 
-__device__ __forceinline__ uint32_t hi_word(double v) {
-    return (uint32_t)((uint64_t)__double_as_longlong(v) >> 32);
+// ---- FP64 <-> FP32 with integer operations (no FP64-pipe instruction) ----------------------
+// Value of (d * 2^e2) rounded to float (round half up), d > 0 an integer below 2^64;
+// 0 when below the float normal range.
+__device__ __forceinline__ float u64_scaled_to_f32(uint64_t d, int e2) {
+    if (d == 0) return 0.0f;
+    const int msb = 63 - __clzll((long long)d);
+    uint32_t mant;
+    int E = msb + e2 + 127;
+    if (msb <= 23) {
+        mant = (uint32_t)(d << (23 - msb));
+    } else {
+        const int sh = msb - 23;
+        uint64_t m = (d >> sh) + ((d >> (sh - 1)) & 1ull);
+        if (m >> 24) { m >>= 1; ++E; }
+        mant = (uint32_t)m;
+    }
+    if (E <= 0) return 0.0f;
+    if (E >= 255) return __int_as_float(0x7F800000);
+    return __int_as_float((E << 23) | (int)(mant & 0x7FFFFFu));
+}
+
+// b - a for b >= a as float.  Exact up to the final rounding when a and b are normal,
+// of the same sign and in the same binade (the common case for sorted neighbours);
+// otherwise through an FP64 subtraction.
+__device__ __forceinline__ float gap_f32(double a, double b) {
+    const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+    const uint32_t ea = (uint32_t)(ba >> 52) & 0x7FFu, eb = (uint32_t)(bb >> 52) & 0x7FFu;
+    if (ea == eb && ea != 0 && ea != 0x7FF && ((ba ^ bb) >> 63) == 0) {
+        const uint64_t d = bb >= ba ? bb - ba : ba - bb;
+        return u64_scaled_to_f32(d, (int)ea - 1075);
+    }
+    return (float)(b - a);
+}
+
+// float(x) for a double with round half up; zero below the float normal range.
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return __int_as_float((int)(sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 1u : 0u)));
+    float mag = u64_scaled_to_f32((b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull), (e ? e : 1) - 1075);
+    return __int_as_float((int)(__float_as_uint(mag) | sign));
+}
+
+// (double)f, exact; float subnormals become 0.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    uint64_t out = (uint64_t)(b & 0x80000000u) << 32;
+    if (e == 0xFFu) out |= 0x7FF0000000000000ull | ((uint64_t)(b & 0x7FFFFFu) << 29);
+    else if (e != 0) out |= ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)out);
 }
 
 // out = a * b + c (complex)
@@ -73,7 +128,7 @@ __device__ __forceinline__ void cmul(Real ar, Real ai, Real br, Real bi, Real& o
     outi = i;
 }
 
-// exp(-tau theta) for any theta >= 0 (FP64), the anchor / span multiplier.
+// exp(-tau theta) for any theta >= 0, the anchor / span multiplier.
 __device__ __forceinline__ void cexp_neg(double tr, double ti, double th, double& mr, double& mi) {
     double mag = exp(-tr * th);
     double sn, cs;
@@ -108,7 +163,16 @@ struct TermConsts<float> {
     __device__ static __forceinline__ uint32_t lim(const SweepConsts& c, int k, int d) { return c.theta_hi_lim_f[k][d]; }
 };
 
-// Taylor degree for term k that covers every theta whose high word is <= hw.
+template <typename Real>
+__device__ __forceinline__ uint32_t theta_hw(Real th);
+template <>
+__device__ __forceinline__ uint32_t theta_hw<double>(double th) {
+    return (uint32_t)((uint64_t)__double_as_longlong(th) >> 32);
+}
+template <>
+__device__ __forceinline__ uint32_t theta_hw<float>(float th) { return __float_as_uint(th); }
+
+// Taylor degree for term k that covers every theta whose bit pattern is <= hw.
 template <typename Real>
 __device__ __forceinline__ int taylor_degree(const SweepConsts& c, int k, uint32_t hw) {
     int deg = kTaylorMax;
@@ -121,8 +185,7 @@ __device__ __forceinline__ int taylor_degree(const SweepConsts& c, int k, uint32
 // exp(-tau_k theta) by a Taylor polynomial of (warp-uniform) degree deg, or by
 // exp/sincos when theta is beyond the largest Taylor threshold.
 template <typename Real>
-__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, uint32_t th_hw, Real& mr,
-                                           Real& mi) {
+__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, Real& mr, Real& mi) {
     Real ar = 0, ai = 0;
 #pragma unroll
     for (int j = kTaylorMax; j >= 1; --j) {
@@ -141,45 +204,33 @@ __device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg,
         mr = Real(1);
         mi = Real(0);
     }
-    if (th_hw > TermConsts<Real>::lim(c, k, kTaylorMax)) {
+    if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, kTaylorMax))
         cexp_neg(TermConsts<Real>::tau_re(c, k), TermConsts<Real>::tau_im(c, k), th, mr, mi);
-    }
 }
 
-template <typename Real>
-__device__ __forceinline__ uint32_t theta_hw(Real th);
-template <>
-__device__ __forceinline__ uint32_t theta_hw<double>(double th) { return hi_word(th); }
-template <>
-__device__ __forceinline__ uint32_t theta_hw<float>(float th) { return (uint32_t)__float_as_uint(th); }
-
-__device__ __forceinline__ void publish_agg(TileDesc* d, double ar, double ai, double z) {
+__device__ __forceinline__ void publish_agg(TileDesc* d, double ar, double ai, double Mr, double Mi) {
     d->agg_re = ar;
     d->agg_im = ai;
-    d->z = z;
+    d->M_re = Mr;
+    d->M_im = Mi;
     __threadfence();
     st_volatile_u32(&d->flag, 1u);
 }
-__device__ __forceinline__ void publish_inc(TileDesc* d, double ar, double ai, double ir, double ii, double z,
-                                            bool with_agg) {
-    if (with_agg) {
-        d->agg_re = ar;
-        d->agg_im = ai;
-        d->z = z;
-    }
+__device__ __forceinline__ void publish_inc(TileDesc* d, double ir, double ii) {
     d->inc_re = ir;
     d->inc_im = ii;
     __threadfence();
     st_volatile_u32(&d->flag, 2u);
 }
 
-// Decoupled look-back over the tiles tile+step, tile+2 step, ... (step = -1 forward,
-// +1 backward) for term k: returns the carry at coordinate zref,
-//     C = sum_j exp(-tau_k s |zref - z_j|) value_j,
-// stopping at the first tile whose inclusive value is published.
-static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile, int step, int64_t tiles, int ne, int k,
-                                       double tr, double ti, double s, double zref, double& cr, double& ci,
-                                       uint32_t* status) {
+// Decoupled look-back for term k over the tiles tile+step, tile+2 step, ... (step = -1
+// forward, +1 backward).  Returns the state at the anchor of the adjacent tile:
+//     C = agg_{t1} + M_{t1} (agg_{t2} + M_{t2} (... + M_{tj} inc_{tj}))
+// walking until the first published inclusive value.  Every M is one tile's span
+// multiplier, computed directly from its anchor coordinates when it was published.
+static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile, int step, int64_t tiles, int ne,
+                                              int k, double& cr, double& ci, uint32_t* status) {
+    double Pr = 1.0, Pi = 0.0;
     cr = 0.0;
     ci = 0.0;
     int64_t j = tile + step;
@@ -187,7 +238,7 @@ static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile
         const TileDesc* d = desc + j * ne + k;
         uint32_t f = ld_volatile_u32(&d->flag);
         if (f == 0) {
-            long long t0 = clock64();
+            const long long t0 = clock64();
             while ((f = ld_volatile_u32(&d->flag)) == 0) {
                 if (clock64() - t0 > kSpinLimitCycles) {
                     atomicOr(status, kStatusTimeout);
@@ -196,24 +247,24 @@ static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile
             }
         }
         __threadfence();
-        double zj = __ldcg(&d->z);
-        double er, ei;
-        cexp_neg(tr, ti, s * fabs(zref - zj), er, ei);
-        double vr = f == 2 ? __ldcg(&d->inc_re) : __ldcg(&d->agg_re);
-        double vi = f == 2 ? __ldcg(&d->inc_im) : __ldcg(&d->agg_im);
-        cfma(er, ei, vr, vi, cr, ci, cr, ci);
-        if (f == 2) return;
+        if (f == 2) {
+            cfma<double>(Pr, Pi, __ldcg(&d->inc_re), __ldcg(&d->inc_im), cr, ci, cr, ci);
+            return;
+        }
+        cfma<double>(Pr, Pi, __ldcg(&d->agg_re), __ldcg(&d->agg_im), cr, ci, cr, ci);
+        cmul<double>(Pr, Pi, __ldcg(&d->M_re), __ldcg(&d->M_im), Pr, Pi);
         j += step;
     }
 }
 
-// Shared-memory footprint of the sweep kernels: coordinates (double), strengths (Real)
-// and the per-term exclusive thread prefixes (Real), padded one slot per R points so
-// that a warp reading one point per thread (stride R) hits distinct banks.
+// Shared-memory layout: coordinates (double), later overwritten by the gaps (Real) and
+// finally by the output; strengths (Real); per-term exclusive thread prefixes (Real).
+// Per-point arrays are padded one slot per R points so that a warp reading one point
+// per thread (stride R) hits distinct banks.
 template <typename Real, int NE, int T, int R>
 struct SweepSmem {
     static constexpr int TILE = T * R;
-    static constexpr int TP = TILE + TILE / R + 1;
+    static constexpr int TP = TILE + TILE / R + 2;
     static constexpr size_t z_off = 0;
     static constexpr size_t al_off = z_off + sizeof(double) * TP;
     static constexpr size_t scan_off = (al_off + sizeof(Real) * TP + 15) / 16 * 16;
@@ -223,50 +274,22 @@ struct SweepSmem {
 template <int R>
 __device__ __forceinline__ int pad(int i) { return i + i / R; }
 
-// Per-term combine of the warp totals, look-back and publication (one lane per term).
-// dir = -1: forward (anchor = last point, carry comes from lower tiles);
-// dir = +1: backward (anchor = first point, carry comes from higher tiles).
-// s_w[k][w] holds each warp's total map (M, F) in the sweep direction; on return
-// s_win[k][w] holds the state entering warp w (after the carry).
-template <int NE, int NW>
-__device__ __forceinline__ void tile_combine(const SweepArgs& a, const SweepConsts& c, TileDesc* desc, int64_t tile,
-                                             int dir, bool first_in_dir, double zanchor, double zref,
-                                             double (*s_w)[NW][4], double (*s_win)[NW][2], int k) {
-    double pre[NW][4];
-    double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        const int ww = dir < 0 ? q : NW - 1 - q;  // sweep order
-        pre[ww][0] = Pr; pre[ww][1] = Pi; pre[ww][2] = Qr; pre[ww][3] = Qi;
-        cfma<double>(s_w[k][ww][0], s_w[k][ww][1], Qr, Qi, s_w[k][ww][2], s_w[k][ww][3], Qr, Qi);
-        cmul<double>(s_w[k][ww][0], s_w[k][ww][1], Pr, Pi, Pr, Pi);
-    }
-    TileDesc* dd = desc + tile * NE + k;
-    double Cr = 0, Ci = 0;
-    const double tr = c.tau_re[k], ti = c.tau_im[k], s = c.s;
-    if (first_in_dir) {
-        publish_inc(dd, Qr, Qi, Qr, Qi, zanchor, true);
-    } else {
-        publish_agg(dd, Qr, Qi, zanchor);
-        look_back(desc, tile, dir, a.tiles, NE, k, tr, ti, s, zref, Cr, Ci, a.status);
-        double Er, Ei;
-        cexp_neg(tr, ti, s * fabs(zanchor - zref), Er, Ei);
-        double Ir, Ii;
-        cfma<double>(Er, Ei, Cr, Ci, Qr, Qi, Ir, Ii);
-        publish_inc(dd, 0, 0, Ir, Ii, zanchor, false);
-    }
-#pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-        double xr, xi;
-        cfma<double>(pre[ww][0], pre[ww][1], Cr, Ci, pre[ww][2], pre[ww][3], xr, xi);
-        s_win[k][ww][0] = xr;
-        s_win[k][ww][1] = xi;
-    }
-}
+template <typename Real>
+__device__ __forceinline__ Real to_real(double v);
+template <>
+__device__ __forceinline__ double to_real<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_real<float>(double v) { return f64_to_f32(v); }
+
+template <typename Real>
+__device__ __forceinline__ Real gap_real(double a, double b, double s, float s_f);
+template <>
+__device__ __forceinline__ double gap_real<double>(double a, double b, double s, float) { return s * (b - a); }
+template <>
+__device__ __forceinline__ float gap_real<float>(double a, double b, double, float s_f) { return s_f * gap_f32(a, b); }
 
 // Stages the tile: coordinates, strengths (0 at targets) and target bits.  Points past
-// the end get z = 0, alpha = 0 and are not targets; n_extra points after the tile
-// (the next tile's first point for the backward sweep) are loaded as coordinates only.
+// the end get z = 0, alpha = 0 and are not targets.
 template <typename Real, int T, int R>
 __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* __restrict__ keys,
                                            const uint32_t* __restrict__ vals, int64_t base, int nvalid,
@@ -284,11 +307,54 @@ __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* _
             else tg = true;
         }
         s_z[pad<R>(i)] = z;
-        s_al[pad<R>(i)] = (Real)al;
+        s_al[pad<R>(i)] = to_real<Real>(al);
         const unsigned b = __ballot_sync(0xffffffffu, tg);
         if (lane == 0) s_tgt[i >> 5] = b;
     }
 }
+
+// Phase B for term k (one lane): combine the warp totals s_w[k][.] in sweep order,
+// publish aggregate + span multiplier, look back, publish the inclusive value, and
+// leave the state entering each warp in s_win[k][.].
+template <int NE, int NW>
+__device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc, int64_t tile, int dir,
+                                             bool first_in_dir, double Mr, double Mi, double (*s_w)[NW][4],
+                                             double (*s_win)[NW][2], int k) {
+    double pre[NW][4];
+    double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int ww = dir < 0 ? q : NW - 1 - q;
+        pre[ww][0] = Pr; pre[ww][1] = Pi; pre[ww][2] = Qr; pre[ww][3] = Qi;
+        cfma<double>(s_w[k][ww][0], s_w[k][ww][1], Qr, Qi, s_w[k][ww][2], s_w[k][ww][3], Qr, Qi);
+        cmul<double>(s_w[k][ww][0], s_w[k][ww][1], Pr, Pi, Pr, Pi);
+    }
+    TileDesc* dd = desc + tile * NE + k;
+    double Cr = 0, Ci = 0;
+    publish_agg(dd, Qr, Qi, Mr, Mi);
+    if (first_in_dir) {
+        publish_inc(dd, Qr, Qi);
+    } else {
+        look_back(desc, tile, dir, a.tiles, NE, k, Cr, Ci, a.status);
+        double Ir, Ii;
+        cfma<double>(Mr, Mi, Cr, Ci, Qr, Qi, Ir, Ii);
+        publish_inc(dd, Ir, Ii);
+    }
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+        double xr, xi;
+        cfma<double>(pre[ww][0], pre[ww][1], Cr, Ci, pre[ww][2], pre[ww][3], xr, xi);
+        s_win[k][ww][0] = xr;
+        s_win[k][ww][1] = xi;
+    }
+}
+
+template <typename Real>
+__device__ __forceinline__ double real_to_f64(Real v);
+template <>
+__device__ __forceinline__ double real_to_f64<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double real_to_f64<float>(float v) { return f32_to_f64(v); }
 
 template <typename Real, int NE, int T, int R>
 __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepConsts c) {
@@ -298,10 +364,12 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     constexpr bool kF64 = sizeof(Real) == 8;
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
+    Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gaps, written over s_z
     Real* s_al = reinterpret_cast<Real*>(smem + SM::al_off);
     Real* s_scan = reinterpret_cast<Real*>(smem + SM::scan_off);  // [NE][4][T]
     __shared__ double s_w[NE][NW][4];
     __shared__ double s_win[NE][NW][2];
+    __shared__ double s_M[NE][2];
     __shared__ uint32_t s_tgt[TILE / 32];
     __shared__ uint32_t s_tile;
     __shared__ double s_zprev;
@@ -319,52 +387,58 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     if (tid == 0) s_zprev = base > 0 ? key_coord(keys[base - 1]) : 0.0;
     __syncthreads();
 
-    // my R points: gaps theta = s (z_i - z_{i-1}) (FP64 difference), target bits
-    const double s = c.s;
     const int i0 = tid * R;
-    const double zprev = s_zprev;
-    Real th[R];
-    uint32_t thw[R];
+    const double zprev = s_zprev, zend = s_z[pad<R>(nvalid - 1)];
+    // gaps of my R points, warp-wide largest gap
+    Real thr[R];
     uint32_t hw = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r;
-        double t = 0.0;
-        if (i < nvalid && base + i > 0) t = s * (s_z[pad<R>(i)] - (i > 0 ? s_z[pad<R>(i - 1)] : zprev));
-        th[r] = (Real)t;
-        thw[r] = theta_hw<Real>(th[r]);
-        hw = max(hw, thw[r]);
+        Real t = 0;
+        if (i < nvalid && base + i > 0)
+            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], c.s, c.s_f);
+        thr[r] = t;
+        hw = max(hw, theta_hw<Real>(t));
     }
     hw = __reduce_max_sync(0xffffffffu, hw);
-    double th_span = 0.0;
+    Real thsp = 0;
     if (i0 < nvalid && (base > 0 || i0 > 0))
-        th_span = s * (s_z[pad<R>(min(i0 + R - 1, nvalid - 1))] - (i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev));
-    const Real thsp = (Real)th_span;
-    const uint32_t thsp_w = theta_hw<Real>(thsp);
-    const uint32_t hsp = __reduce_max_sync(0xffffffffu, thsp_w);
+        thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], c.s,
+                              c.s_f);
+    const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) s_th[pad<R>(i0 + r)] = thr[r];
     uint32_t tmask = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
-    const double zend = s_z[pad<R>(nvalid - 1)];
+    // the tile's span multipliers (lanes of the last warp, one per term)
+    if (tid >= T - NE && tile > 0) {
+        const int k = tid - (T - NE);
+        double mr, mi;
+        cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (zend - zprev), mr, mi);
+        s_M[k][0] = mr;
+        s_M[k][1] = mi;
+    }
 
     // phase A: per term, thread aggregates and the warp scan
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
         const int deg = taylor_degree<Real>(c, k, hw);
-        Real mr[R], mi[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
-        if constexpr (kF64) {
-            double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (i0 + r < nvalid) mt[r] = make_double2((double)mr[r], (double)mi[r]);
+        double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
+        Real fr = 0, fi = 0;
+#pragma unroll 4
+        for (int r = 0; r < R; ++r) {
+            Real mr, mi;
+            multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
+            if constexpr (kF64) {
+                if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
+            }
+            cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
         }
-        Real fr = s_al[pad<R>(i0)], fi = 0;
-#pragma unroll
-        for (int r = 1; r < R; ++r) cfma<Real>(mr[r], mi[r], fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
         Real Mr, Mi;
-        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, thsp_w, Mr, Mi);
+        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Real Mor = __shfl_up_sync(0xffffffffu, Mr, o), Moi = __shfl_up_sync(0xffffffffu, Mi, o);
@@ -380,13 +454,15 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         Real* sc = s_scan + (size_t)k * 4 * T;
         sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 31) {
-            s_w[k][w][0] = (double)Mr; s_w[k][w][1] = (double)Mi;
-            s_w[k][w][2] = (double)fr; s_w[k][w][3] = (double)fi;
+            s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+            s_w[k][w][2] = real_to_f64<Real>(fr); s_w[k][w][3] = real_to_f64<Real>(fi);
         }
     }
     __syncthreads();
     // phase B: one lane per term joins the warps and the tiles
-    if (tid < NE) tile_combine<NE, NW>(a, c, a.fdesc, tile, -1, tile == 0, zend, zprev, s_w, s_win, tid);
+    if (tid < NE)
+        tile_combine<NE, NW>(a, a.fdesc, tile, -1, tile == 0, tile > 0 ? s_M[tid][0] : 1.0,
+                             tile > 0 ? s_M[tid][1] : 0.0, s_w, s_win, tid);
     __syncthreads();
     // phase C: apply the carries, final pass, evaluation at targets
     Real acc[R];
@@ -396,35 +472,41 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     for (int k = 0; k < NE; ++k) {
         const Real* sc = s_scan + (size_t)k * 4 * T;
         Real fr, fi;
-        cfma<Real>(sc[tid], sc[T + tid], (Real)s_win[k][w][0], (Real)s_win[k][w][1], sc[2 * T + tid],
-                   sc[3 * T + tid], fr, fi);
-        Real mr[R], mi[R];
-        if constexpr (kF64) {
-            const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
-                mr[r] = (Real)m.x;
-                mi[r] = (Real)m.y;
-            }
-        } else {
-            const int deg = taylor_degree<Real>(c, k, hw);
-#pragma unroll
-            for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
-        }
+        cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                   sc[2 * T + tid], sc[3 * T + tid], fr, fi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
+        const int deg = taylor_degree<Real>(c, k, hw);
+        const double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            cfma<Real>(mr[r], mi[r], fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+            Real mr, mi;
+            if constexpr (kF64) {
+                const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
+                mr = m.x;
+                mi = m.y;
+            } else {
+                multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
+            }
+            cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
             if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
         }
     }
     // forward partial sums, written coalesced through shared memory
     __syncthreads();
+    if constexpr (kF64) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = (double)acc[r];
-    __syncthreads();
-    for (int i = tid; i < nvalid; i += T) a.fwd[base + i] = s_z[pad<R>(i)];
+        for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = acc[r];
+        __syncthreads();
+        double* __restrict__ fwd = static_cast<double*>(a.fwd);
+        for (int i = tid; i < nvalid; i += T) fwd[base + i] = s_z[pad<R>(i)];
+    } else {
+        float* s_o = reinterpret_cast<float*>(s_z);
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_o[pad<R>(i0 + r)] = acc[r];
+        __syncthreads();
+        float* __restrict__ fwd = static_cast<float*>(a.fwd);
+        for (int i = tid; i < nvalid; i += T) fwd[base + i] = s_o[pad<R>(i)];
+    }
 }
 
 template <typename Real, int NE, int T, int R>
@@ -435,10 +517,12 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     constexpr bool kF64 = sizeof(Real) == 8;
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
+    Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gap between points i and i+1, over s_z
     Real* s_al = reinterpret_cast<Real*>(smem + SM::al_off);
     Real* s_scan = reinterpret_cast<Real*>(smem + SM::scan_off);
     __shared__ double s_w[NE][NW][4];
     __shared__ double s_win[NE][NW][2];
+    __shared__ double s_M[NE][2];
     __shared__ uint32_t s_tgt[TILE / 32];
     __shared__ uint32_t s_tile;
 
@@ -456,64 +540,70 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     if (tid == 0) s_z[pad<R>(TILE)] = has_next ? key_coord(keys[base + TILE]) : 0.0;
     __syncthreads();
 
-    const double s = c.s;
     const int i0 = tid * R;
     const double znext = s_z[pad<R>(TILE)], zfirst = s_z[0];
-    // th[r]: gap between points i0+r and i0+r+1 (the FP64 path reads the stored multipliers)
-    Real th[R];
-    uint32_t thw[R];
     uint32_t hw = 0;
+    Real thr[R];
     if constexpr (!kF64) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = i0 + r;
-            double t = 0.0;
-            if (i + 1 < nvalid || (i + 1 == TILE && has_next)) t = s * (s_z[pad<R>(i + 1)] - s_z[pad<R>(i)]);
-            th[r] = (Real)t;
-            thw[r] = theta_hw<Real>(th[r]);
-            hw = max(hw, thw[r]);
+            Real t = 0;
+            if (i + 1 < nvalid || (i + 1 == TILE && has_next))
+                t = gap_real<Real>(s_z[pad<R>(i)], s_z[pad<R>(i + 1)], c.s, c.s_f);
+            thr[r] = t;
+            hw = max(hw, theta_hw<Real>(t));
         }
         hw = __reduce_max_sync(0xffffffffu, hw);
     }
-    double th_span = 0.0;
+    Real thsp = 0;
     {
         const int inext = i0 + R;
         if (i0 < nvalid && (inext < nvalid || (inext == TILE && has_next)))
-            th_span = s * (s_z[pad<R>(inext)] - s_z[pad<R>(i0)]);
+            thsp = gap_real<Real>(s_z[pad<R>(i0)], s_z[pad<R>(inext)], c.s, c.s_f);
     }
-    const Real thsp = (Real)th_span;
-    const uint32_t thsp_w = theta_hw<Real>(thsp);
-    const uint32_t hsp = __reduce_max_sync(0xffffffffu, thsp_w);
+    const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
+    __syncthreads();
+    if constexpr (!kF64) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_th[pad<R>(i0 + r)] = thr[r];
+    }
     uint32_t tmask = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
+    if (tid >= T - NE && has_next) {
+        const int k = tid - (T - NE);
+        double mr, mi;
+        cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (znext - zfirst), mr, mi);
+        s_M[k][0] = mr;
+        s_M[k][1] = mi;
+    }
 
-    auto load_mult = [&](int k, Real* mr, Real* mi) {
+    // multiplier between points i0+r and i0+r+1
+    auto mult_at = [&](int k, int deg, int r, Real& mr, Real& mi) {
         if constexpr (kF64) {
-            const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0 + 1;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int64_t p = base + i0 + r + 1;
-                double2 m = p < a.P ? mt[r] : make_double2(0.0, 0.0);
-                mr[r] = (Real)m.x;
-                mi[r] = (Real)m.y;
-            }
+            const int64_t p = base + i0 + r + 1;
+            const double2 m = p < a.P ? a.mult[(int64_t)k * a.P + p] : make_double2(0.0, 0.0);
+            mr = m.x;
+            mi = m.y;
         } else {
-            const int deg = taylor_degree<Real>(c, k, hw);
-#pragma unroll
-            for (int r = 0; r < R; ++r) multiplier<Real>(c, k, deg, th[r], thw[r], mr[r], mi[r]);
+            multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
         }
     };
 
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
-        Real mr[R], mi[R];
-        load_mult(k, mr, mi);
-        Real br = s_al[pad<R>(i0 + R - 1)], bi = 0;
-#pragma unroll
-        for (int r = R - 2; r >= 0; --r) cfma<Real>(mr[r], mi[r], br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+        const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+        Real br = 0, bi = 0;
+#pragma unroll 4
+        for (int r = R - 1; r >= 0; --r) {
+            Real mr, mi;
+            mult_at(k, deg, r, mr, mi);
+            // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
+            cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+        }
         Real Mr, Mi;
-        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, thsp_w, Mr, Mi);
+        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Real Mor = __shfl_down_sync(0xffffffffu, Mr, o), Moi = __shfl_down_sync(0xffffffffu, Mi, o);
@@ -529,12 +619,14 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         Real* sc = s_scan + (size_t)k * 4 * T;
         sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 0) {
-            s_w[k][w][0] = (double)Mr; s_w[k][w][1] = (double)Mi;
-            s_w[k][w][2] = (double)br; s_w[k][w][3] = (double)bi;
+            s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+            s_w[k][w][2] = real_to_f64<Real>(br); s_w[k][w][3] = real_to_f64<Real>(bi);
         }
     }
     __syncthreads();
-    if (tid < NE) tile_combine<NE, NW>(a, c, a.bdesc, tile, +1, !has_next, zfirst, znext, s_w, s_win, tid);
+    if (tid < NE)
+        tile_combine<NE, NW>(a, a.bdesc, tile, +1, !has_next, has_next ? s_M[tid][0] : 1.0,
+                             has_next ? s_M[tid][1] : 0.0, s_w, s_win, tid);
     __syncthreads();
     Real acc[R];
 #pragma unroll
@@ -543,26 +635,39 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     for (int k = 0; k < NE; ++k) {
         const Real* sc = s_scan + (size_t)k * 4 * T;
         Real br, bi;  // state at the first point of the next thread
-        cfma<Real>(sc[tid], sc[T + tid], (Real)s_win[k][w][0], (Real)s_win[k][w][1], sc[2 * T + tid],
-                   sc[3 * T + tid], br, bi);
-        Real mr[R], mi[R];
-        load_mult(k, mr, mi);
+        cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                   sc[2 * T + tid], sc[3 * T + tid], br, bi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
+        const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
 #pragma unroll
         for (int r = R - 1; r >= 0; --r) {
-            cfma<Real>(mr[r], mi[r], br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+            Real mr, mi;
+            mult_at(k, deg, r, mr, mi);
+            cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
             if ((tmask >> r) & 1u) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
         }
     }
     __syncthreads();
+    if constexpr (kF64) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = (double)acc[r];
+        for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = acc[r];
+    } else {
+        float* s_o = reinterpret_cast<float*>(s_z);
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_o[pad<R>(i0 + r)] = acc[r];
+    }
     __syncthreads();
     for (int i = tid; i < nvalid; i += T) {
         if ((s_tgt[i >> 5] >> (i & 31)) & 1u) {
             const int64_t p = base + i;
             const uint32_t v = vals[p];
-            a.u[(int64_t)v - a.N] = a.fwd[p] + s_z[pad<R>(i)];
+            double out;
+            if constexpr (kF64) {
+                out = static_cast<const double*>(a.fwd)[p] + s_z[pad<R>(i)];
+            } else {
+                out = f32_to_f64(static_cast<const float*>(a.fwd)[p] + reinterpret_cast<float*>(s_z)[pad<R>(i)]);
+            }
+            a.u[(int64_t)v - a.N] = out;
         }
     }
 }

@@ -1,10 +1,10 @@
-// FP64 instantiations of the sweep kernels (tile = 128 threads x 16 points).
+// FP64 instantiations of the sweep kernels (tile = 128 threads x 32 points).
 #include "sweep.cuh"
 
 namespace fgt1d {
 
 namespace {
-constexpr int kT = 128, kR = 16;
+constexpr int kT = 128, kR = 32;
 
 template <int NE>
 cudaError_t run(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {

@@ -10,7 +10,7 @@
 // run-length counting keeps the near-constant high digits off the shared atomics);
 // a one-block kernel turns the counts into bucket offsets and a device-side pass plan
 // that skips digits with a single populated bucket; then one "onesweep" kernel per
-// digit ranks a 4096-key tile in shared memory (warp match-any ranking), finds the
+// digit ranks a 4096-key tile in shared memory (ballot-based warp ranking), finds the
 // tile's global offsets by decoupled look-back over the preceding tiles, and writes
 // keys and merged indices out through a shared-memory reorder so that every bucket
 // run is written contiguously.  The pass plan lives on the device, so the whole sort
@@ -194,23 +194,25 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
             val[j] = 0;
         }
     }
-    // stable warp ranking per slot
+    // stable warp ranking per slot: the lanes holding the same digit are found with
+    // eight ballots (one per digit bit); every lane reads the warp's running count for
+    // its digit, then the lowest peer adds the slot's count
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
         const int li = w * 32 * kSortIPT + j * 32 + lane;
         const bool valid = li < nvalid;
-        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned m = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+            peers &= ((dg >> b) & 1u) ? m : ~m;
+        }
+        uint32_t old = valid ? sm.wcnt[w][dg] : 0u;
+        __syncwarp();
         if (valid) {
-            const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-            const unsigned peers = __match_any_sync(vmask, dg);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (lane == leader) {
-                old = sm.wcnt[w][dg];
-                sm.wcnt[w][dg] = old + __popc(peers);
-            }
-            old = __shfl_sync(peers, old, leader);
             rank[j] = old + __popc(peers & lanemask_lt());
+            if ((peers & lanemask_lt()) == 0) sm.wcnt[w][dg] = old + __popc(peers);
         }
         __syncwarp();
     }
@@ -246,8 +248,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
         __syncthreads();
         sm.tile_start[tid] = wpre + inc - v;
     }
-    // decoupled look-back for this digit's global base
+    // decoupled look-back for this digit's global base; each round issues the loads of
+    // kLookAhead predecessors at once so the walk costs one round trip per kLookAhead tiles
     {
+        constexpr int kLookAhead = 16;
         const int dg = tid;
         uint64_t* desc = a.desc + (size_t)d * a.desc_stride;
         uint32_t excl = 0;
@@ -256,20 +260,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
         } else {
             st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescAgg | (uint64_t)tot);
             int64_t j = (int64_t)tile - 1;
-            long long t0 = clock64();
-            while (true) {
-                uint64_t v = ld_volatile_u64(&desc[(size_t)j * 256 + dg]);
-                uint64_t flag = v >> 62;
-                if (flag == 0) {
-                    if (clock64() - t0 > kSpinLimitCycles) {
-                        atomicOr(a.status, kStatusTimeout);
-                        break;
+            bool done = false;
+            while (!done) {
+                uint64_t v[kLookAhead];
+#pragma unroll
+                for (int q = 0; q < kLookAhead; ++q)
+                    v[q] = (j - q >= 0) ? ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg]) : kDescInc;
+#pragma unroll
+                for (int q = 0; q < kLookAhead; ++q) {
+                    if (done) break;
+                    uint64_t x = v[q];
+                    if ((x >> 62) == 0) {
+                        const long long t0 = clock64();
+                        while (((x = ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg])) >> 62) == 0) {
+                            if (clock64() - t0 > kSpinLimitCycles) {
+                                atomicOr(a.status, kStatusTimeout);
+                                x = kDescInc;
+                                break;
+                            }
+                        }
                     }
-                    continue;
+                    excl += (uint32_t)(x & 0xFFFFFFFFull);
+                    if ((x >> 62) == 2) done = true;
                 }
-                excl += (uint32_t)(v & 0xFFFFFFFFull);
-                if (flag == 2 || j == 0) break;
-                --j;
+                j -= kLookAhead;
             }
             st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)(excl + tot));
         }

@@ -17,11 +17,12 @@
 // one lane per term joins the warps and the tiles.  Per tile the kernel runs
 //   phase A  per term: multipliers, thread aggregates, warp scans (exclusive prefixes
 //            kept in shared memory);
-//   phase B  per term (one lane each): combine the warp totals, publish the tile
+//   phase B  per term (one warp each): combine the warp totals, publish the tile
 //            aggregate with the tile's span multiplier exp(-tau s (z_anchor - z_prev))
 //            computed directly from the FP64 anchor coordinates, decoupled look-back
-//            over the neighbouring tiles (one complex multiply-add per predecessor,
-//            using the published span multipliers), publish the inclusive value;
+//            over the neighbouring tiles 32 at a time (a complex multiply-add per
+//            predecessor, using the published span multipliers), publish the
+//            inclusive value;
 //   phase C  per term: apply the carries, final pass, evaluation at targets.
 // Per-point multipliers use a Taylor polynomial of warp-uniform degree chosen from
 // the warp's largest gap (integer compares on the bit pattern of theta), falling back
@@ -38,6 +39,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "fgt1d_internal.h"
 #include "kernels.h"
@@ -172,40 +175,81 @@ __device__ __forceinline__ uint32_t theta_hw<double>(double th) {
 template <>
 __device__ __forceinline__ uint32_t theta_hw<float>(float th) { return __float_as_uint(th); }
 
+template <typename Real>
+struct MaxDegree;
+
 // Taylor degree for term k that covers every theta whose bit pattern is <= hw.
 template <typename Real>
 __device__ __forceinline__ int taylor_degree(const SweepConsts& c, int k, uint32_t hw) {
-    int deg = kTaylorMax;
+    int deg = MaxDegree<Real>::value;
 #pragma unroll
-    for (int d = kTaylorMax - 1; d >= 0; --d)
+    for (int d = MaxDegree<Real>::value - 1; d >= 0; --d)
         if (hw <= TermConsts<Real>::lim(c, k, d)) deg = d;
     return deg;
 }
 
-// exp(-tau_k theta) by a Taylor polynomial of (warp-uniform) degree deg, or by
-// exp/sincos when theta is beyond the largest Taylor threshold.
 template <typename Real>
-__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, Real& mr, Real& mi) {
-    Real ar = 0, ai = 0;
+struct MaxDegree;
+template <>
+struct MaxDegree<double> { static constexpr int value = kTaylorMax; };
+template <>
+struct MaxDegree<float> { static constexpr int value = 8; };
+
+// exp(-tau_k theta) by a Taylor polynomial of compile-time degree D (Horner, complex
+// coefficients, real theta).  At the largest degree, points beyond its threshold fall
+// back to exp/sincos; below it the warp-uniform degree already covers every point.
+template <typename Real, int D>
+__device__ __forceinline__ void taylor(const SweepConsts& c, int k, Real th, Real& mr, Real& mi) {
+    if constexpr (D == 0) {
+        mr = Real(1);
+        mi = Real(0);
+    } else {
+        Real ar = TermConsts<Real>::tc_re(c, k, D), ai = TermConsts<Real>::tc_im(c, k, D);
 #pragma unroll
-    for (int j = kTaylorMax; j >= 1; --j) {
-        if (j == deg) {
-            ar = TermConsts<Real>::tc_re(c, k, j);
-            ai = TermConsts<Real>::tc_im(c, k, j);
-        } else if (j < deg) {
+        for (int j = D - 1; j >= 1; --j) {
             ar = fma(ar, th, TermConsts<Real>::tc_re(c, k, j));
             ai = fma(ai, th, TermConsts<Real>::tc_im(c, k, j));
         }
-    }
-    if (deg >= 1) {
         mr = fma(ar, th, Real(1));
         mi = ai * th;
-    } else {
-        mr = Real(1);
-        mi = Real(0);
     }
-    if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, kTaylorMax))
-        cexp_neg(TermConsts<Real>::tau_re(c, k), TermConsts<Real>::tau_im(c, k), th, mr, mi);
+    if constexpr (D == MaxDegree<Real>::value) {
+        if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D))
+            cexp_neg(TermConsts<Real>::tau_re(c, k), TermConsts<Real>::tau_im(c, k), th, mr, mi);
+    }
+}
+
+// Runs body(integral_constant<int, D>) for the warp-uniform degree deg.
+template <typename Real, typename Body>
+__device__ __forceinline__ void with_degree(int deg, Body&& body) {
+    switch (deg) {
+        case 0: body(std::integral_constant<int, 0>{}); break;
+        case 1: body(std::integral_constant<int, 1>{}); break;
+        case 2: body(std::integral_constant<int, 2>{}); break;
+        case 3: body(std::integral_constant<int, 3>{}); break;
+        case 4: body(std::integral_constant<int, 4>{}); break;
+        case 5: body(std::integral_constant<int, 5>{}); break;
+        case 6: body(std::integral_constant<int, 6>{}); break;
+        case 7: body(std::integral_constant<int, 7>{}); break;
+        default:
+            if constexpr (MaxDegree<Real>::value == 8) {
+                body(std::integral_constant<int, 8>{});
+            } else {
+                switch (deg) {
+                    case 8: body(std::integral_constant<int, 8>{}); break;
+                    case 9: body(std::integral_constant<int, 9>{}); break;
+                    case 10: body(std::integral_constant<int, 10>{}); break;
+                    case 11: body(std::integral_constant<int, 11>{}); break;
+                    default: body(std::integral_constant<int, MaxDegree<Real>::value>{}); break;
+                }
+            }
+    }
+}
+
+// Single multiplier with a runtime degree (thread and tile spans).
+template <typename Real>
+__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, Real& mr, Real& mi) {
+    with_degree<Real>(deg, [&](auto Dc) { taylor<Real, decltype(Dc)::value>(c, k, th, mr, mi); });
 }
 
 __device__ __forceinline__ void publish_agg(TileDesc* d, double ar, double ai, double Mr, double Mi) {
@@ -223,38 +267,77 @@ __device__ __forceinline__ void publish_inc(TileDesc* d, double ir, double ii) {
     st_volatile_u32(&d->flag, 2u);
 }
 
-// Decoupled look-back for term k over the tiles tile+step, tile+2 step, ... (step = -1
-// forward, +1 backward).  Returns the state at the anchor of the adjacent tile:
+// Decoupled look-back for term k by one warp over the tiles tile+dir, tile+2 dir, ...
+// (dir = -1 forward, +1 backward), 32 tiles per round trip.  Returns (in every lane)
+// the state at the anchor of the adjacent tile:
 //     C = agg_{t1} + M_{t1} (agg_{t2} + M_{t2} (... + M_{tj} inc_{tj}))
-// walking until the first published inclusive value.  Every M is one tile's span
-// multiplier, computed directly from its anchor coordinates when it was published.
-static __device__ __noinline__ void look_back(const TileDesc* desc, int64_t tile, int step, int64_t tiles, int ne,
-                                              int k, double& cr, double& ci, uint32_t* status) {
-    double Pr = 1.0, Pi = 0.0;
-    cr = 0.0;
-    ci = 0.0;
-    int64_t j = tile + step;
-    while (j >= 0 && j < tiles) {
-        const TileDesc* d = desc + j * ne + k;
-        uint32_t f = ld_volatile_u32(&d->flag);
-        if (f == 0) {
-            const long long t0 = clock64();
-            while ((f = ld_volatile_u32(&d->flag)) == 0) {
-                if (clock64() - t0 > kSpinLimitCycles) {
-                    atomicOr(status, kStatusTimeout);
-                    return;
+// up to the nearest tile whose inclusive value is published.  Every M is one tile's
+// span multiplier, computed directly from its anchor coordinates when it was published;
+// within a round the products of M are formed by a lane prefix scan.
+static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t tile, int dir, int64_t tiles, int ne,
+                                                   int k, double& Cr, double& Ci, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    double Pr = 1.0, Pi = 0.0;  // product of the span multipliers of the tiles consumed so far
+    Cr = 0.0;
+    Ci = 0.0;
+    int64_t jb = tile + dir;
+    bool timed_out = false;
+    while (true) {
+        const int64_t j = jb + (int64_t)dir * lane;
+        const bool valid = j >= 0 && j < tiles;
+        const TileDesc* d = desc + (valid ? j : 0) * ne + k;
+        uint32_t f = 2;
+        if (valid) {
+            f = ld_volatile_u32(&d->flag);
+            if (f == 0) {
+                const long long t0 = clock64();
+                while ((f = ld_volatile_u32(&d->flag)) == 0) {
+                    if (clock64() - t0 > kSpinLimitCycles) {
+                        timed_out = true;
+                        f = 2;
+                        break;
+                    }
                 }
             }
         }
         __threadfence();
-        if (f == 2) {
-            cfma<double>(Pr, Pi, __ldcg(&d->inc_re), __ldcg(&d->inc_im), cr, ci, cr, ci);
-            return;
+        double vr = 0.0, vi = 0.0, mr = 1.0, mi = 0.0;
+        if (valid && !timed_out) {
+            if (f == 2) {
+                vr = __ldcg(&d->inc_re);
+                vi = __ldcg(&d->inc_im);
+            } else {
+                vr = __ldcg(&d->agg_re);
+                vi = __ldcg(&d->agg_im);
+            }
+            mr = __ldcg(&d->M_re);
+            mi = __ldcg(&d->M_im);
         }
-        cfma<double>(Pr, Pi, __ldcg(&d->agg_re), __ldcg(&d->agg_im), cr, ci, cr, ci);
-        cmul<double>(Pr, Pi, __ldcg(&d->M_re), __ldcg(&d->M_im), Pr, Pi);
-        j += step;
+        const unsigned incm = __ballot_sync(0xffffffffu, f == 2);
+        const int last = incm ? __ffs(incm) - 1 : 31;
+        // inclusive prefix product of M over lanes, then exclusive
+        double Er = mr, Ei = mi;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double orr = __shfl_up_sync(0xffffffffu, Er, o), oi = __shfl_up_sync(0xffffffffu, Ei, o);
+            if (lane >= o) cmul<double>(Er, Ei, orr, oi, Er, Ei);
+        }
+        double Xr = __shfl_up_sync(0xffffffffu, Er, 1), Xi = __shfl_up_sync(0xffffffffu, Ei, 1);
+        if (lane == 0) { Xr = 1.0; Xi = 0.0; }
+        double tr = 0.0, ti = 0.0;
+        if (lane <= last) cmul<double>(Xr, Xi, vr, vi, tr, ti);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            ti += __shfl_xor_sync(0xffffffffu, ti, o);
+        }
+        cfma<double>(Pr, Pi, tr, ti, Cr, Ci, Cr, Ci);
+        if (incm) break;
+        const double Lr = __shfl_sync(0xffffffffu, Er, 31), Li = __shfl_sync(0xffffffffu, Ei, 31);
+        cmul<double>(Pr, Pi, Lr, Li, Pr, Pi);
+        jb += 32 * (int64_t)dir;
     }
+    if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(status, kStatusTimeout);
 }
 
 // Shared-memory layout: coordinates (double), later overwritten by the gaps (Real) and
@@ -313,39 +396,42 @@ __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* _
     }
 }
 
-// Phase B for term k (one lane): combine the warp totals s_w[k][.] in sweep order,
+// Phase B for term k by one warp: combine the warp totals s_w[k][.] in sweep order,
 // publish aggregate + span multiplier, look back, publish the inclusive value, and
 // leave the state entering each warp in s_win[k][.].
 template <int NE, int NW>
 __device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc, int64_t tile, int dir,
                                              bool first_in_dir, double Mr, double Mi, double (*s_w)[NW][4],
                                              double (*s_win)[NW][2], int k) {
-    double pre[NW][4];
+    const int lane = threadIdx.x & 31;
     double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
+    double pre0 = 1, pre1 = 0, pre2 = 0, pre3 = 0;  // prefix before warp `lane` (lanes < NW)
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
         const int ww = dir < 0 ? q : NW - 1 - q;
-        pre[ww][0] = Pr; pre[ww][1] = Pi; pre[ww][2] = Qr; pre[ww][3] = Qi;
+        if (ww == lane) { pre0 = Pr; pre1 = Pi; pre2 = Qr; pre3 = Qi; }
         cfma<double>(s_w[k][ww][0], s_w[k][ww][1], Qr, Qi, s_w[k][ww][2], s_w[k][ww][3], Qr, Qi);
         cmul<double>(s_w[k][ww][0], s_w[k][ww][1], Pr, Pi, Pr, Pi);
     }
     TileDesc* dd = desc + tile * NE + k;
     double Cr = 0, Ci = 0;
-    publish_agg(dd, Qr, Qi, Mr, Mi);
+    if (lane == 0) publish_agg(dd, Qr, Qi, Mr, Mi);
+    __syncwarp();
     if (first_in_dir) {
-        publish_inc(dd, Qr, Qi);
+        if (lane == 0) publish_inc(dd, Qr, Qi);
     } else {
-        look_back(desc, tile, dir, a.tiles, NE, k, Cr, Ci, a.status);
-        double Ir, Ii;
-        cfma<double>(Mr, Mi, Cr, Ci, Qr, Qi, Ir, Ii);
-        publish_inc(dd, Ir, Ii);
+        look_back_warp(desc, tile, dir, a.tiles, NE, k, Cr, Ci, a.status);
+        if (lane == 0) {
+            double Ir, Ii;
+            cfma<double>(Mr, Mi, Cr, Ci, Qr, Qi, Ir, Ii);
+            publish_inc(dd, Ir, Ii);
+        }
     }
-#pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
+    if (lane < NW) {
         double xr, xi;
-        cfma<double>(pre[ww][0], pre[ww][1], Cr, Ci, pre[ww][2], pre[ww][3], xr, xi);
-        s_win[k][ww][0] = xr;
-        s_win[k][ww][1] = xi;
+        cfma<double>(pre0, pre1, Cr, Ci, pre2, pre3, xr, xi);
+        s_win[k][lane][0] = xr;
+        s_win[k][lane][1] = xi;
     }
 }
 
@@ -428,15 +514,17 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         const int deg = taylor_degree<Real>(c, k, hw);
         double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
         Real fr = 0, fi = 0;
+        with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll 4
-        for (int r = 0; r < R; ++r) {
-            Real mr, mi;
-            multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
-            if constexpr (kF64) {
-                if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
+            for (int r = 0; r < R; ++r) {
+                Real mr, mi;
+                taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
+                if constexpr (kF64) {
+                    if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
+                }
+                cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
             }
-            cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-        }
+        });
         Real Mr, Mi;
         multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
 #pragma unroll
@@ -460,9 +548,9 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     }
     __syncthreads();
     // phase B: one lane per term joins the warps and the tiles
-    if (tid < NE)
-        tile_combine<NE, NW>(a, a.fdesc, tile, -1, tile == 0, tile > 0 ? s_M[tid][0] : 1.0,
-                             tile > 0 ? s_M[tid][1] : 0.0, s_w, s_win, tid);
+    for (int k = w; k < NE; k += NW)
+        tile_combine<NE, NW>(a, a.fdesc, tile, -1, tile == 0, tile > 0 ? s_M[k][0] : 1.0, tile > 0 ? s_M[k][1] : 0.0,
+                             s_w, s_win, k);
     __syncthreads();
     // phase C: apply the carries, final pass, evaluation at targets
     Real acc[R];
@@ -475,20 +563,24 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
                    sc[2 * T + tid], sc[3 * T + tid], fr, fi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        const int deg = taylor_degree<Real>(c, k, hw);
-        const double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
+        if constexpr (kF64) {
+            const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            Real mr, mi;
-            if constexpr (kF64) {
+            for (int r = 0; r < R; ++r) {
                 const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
-                mr = m.x;
-                mi = m.y;
-            } else {
-                multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
+                cfma<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+                if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
             }
-            cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-            if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+        } else {
+            with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    Real mr, mi;
+                    taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
+                    cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+                    if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+                }
+            });
         }
     }
     // forward partial sums, written coalesced through shared memory
@@ -579,15 +671,16 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         s_M[k][1] = mi;
     }
 
-    // multiplier between points i0+r and i0+r+1
-    auto mult_at = [&](int k, int deg, int r, Real& mr, Real& mi) {
+    // multiplier between points i0+r and i0+r+1 (stored table, or a Taylor polynomial
+    // of compile-time degree D on the FP32 path)
+    auto mult_at = [&](int k, auto Dc, int r, Real& mr, Real& mi) {
         if constexpr (kF64) {
             const int64_t p = base + i0 + r + 1;
             const double2 m = p < a.P ? a.mult[(int64_t)k * a.P + p] : make_double2(0.0, 0.0);
             mr = m.x;
             mi = m.y;
         } else {
-            multiplier<Real>(c, k, deg, s_th[pad<R>(i0 + r)], mr, mi);
+            taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
         }
     };
 
@@ -595,13 +688,15 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     for (int k = 0; k < NE; ++k) {
         const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
         Real br = 0, bi = 0;
+        with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll 4
-        for (int r = R - 1; r >= 0; --r) {
-            Real mr, mi;
-            mult_at(k, deg, r, mr, mi);
-            // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
-            cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
-        }
+            for (int r = R - 1; r >= 0; --r) {
+                Real mr, mi;
+                mult_at(k, Dc, r, mr, mi);
+                // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
+                cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+            }
+        });
         Real Mr, Mi;
         multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
 #pragma unroll
@@ -624,9 +719,9 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         }
     }
     __syncthreads();
-    if (tid < NE)
-        tile_combine<NE, NW>(a, a.bdesc, tile, +1, !has_next, has_next ? s_M[tid][0] : 1.0,
-                             has_next ? s_M[tid][1] : 0.0, s_w, s_win, tid);
+    for (int k = w; k < NE; k += NW)
+        tile_combine<NE, NW>(a, a.bdesc, tile, +1, !has_next, has_next ? s_M[k][0] : 1.0, has_next ? s_M[k][1] : 0.0,
+                             s_w, s_win, k);
     __syncthreads();
     Real acc[R];
 #pragma unroll
@@ -639,13 +734,15 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                    sc[2 * T + tid], sc[3 * T + tid], br, bi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
         const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+        with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll
-        for (int r = R - 1; r >= 0; --r) {
-            Real mr, mi;
-            mult_at(k, deg, r, mr, mi);
-            cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
-            if ((tmask >> r) & 1u) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
-        }
+            for (int r = R - 1; r >= 0; --r) {
+                Real mr, mi;
+                mult_at(k, Dc, r, mr, mi);
+                cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+                if ((tmask >> r) & 1u) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+            }
+        });
     }
     __syncthreads();
     if constexpr (kF64) {

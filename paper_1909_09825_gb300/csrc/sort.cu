@@ -152,7 +152,7 @@ struct SortSmem {
     uint32_t tile_id;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d) {
     const SortPlan* pl = a.plan;
     if (!pl->active[d]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -195,24 +195,33 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
         }
     }
     // stable warp ranking per slot: the lanes holding the same digit are found with
-    // eight ballots (one per digit bit); every lane reads the warp's running count for
-    // its digit, then the lowest peer adds the slot's count
+    // eight ballots (one per digit bit), for all slots first (independent work); then,
+    // slot by slot, every lane reads the warp's running count for its digit and the
+    // lowest peer adds the slot's count
+    unsigned peers[kSortIPT];
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        const int li = w * 32 * kSortIPT + j * 32 + lane;
+        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+        unsigned pm = __ballot_sync(0xffffffffu, li < nvalid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned m = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+            pm &= ((dg >> b) & 1u) ? m : ~m;
+        }
+        peers[j] = pm;
+    }
+    const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
         const int li = w * 32 * kSortIPT + j * 32 + lane;
         const bool valid = li < nvalid;
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned m = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
-            peers &= ((dg >> b) & 1u) ? m : ~m;
-        }
-        uint32_t old = valid ? sm.wcnt[w][dg] : 0u;
+        const uint32_t old = valid ? sm.wcnt[w][dg] : 0u;
         __syncwarp();
         if (valid) {
-            rank[j] = old + __popc(peers & lanemask_lt());
-            if ((peers & lanemask_lt()) == 0) sm.wcnt[w][dg] = old + __popc(peers);
+            rank[j] = old + __popc(peers[j] & lt);
+            if ((peers[j] & lt) == 0) sm.wcnt[w][dg] = old + __popc(peers[j]);
         }
         __syncwarp();
     }
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(SortArgs a, int d) {
     // decoupled look-back for this digit's global base; each round issues the loads of
     // kLookAhead predecessors at once so the walk costs one round trip per kLookAhead tiles
     {
-        constexpr int kLookAhead = 16;
+        constexpr int kLookAhead = 8;
         const int dg = tid;
         uint64_t* desc = a.desc + (size_t)d * a.desc_stride;
         uint32_t excl = 0;

@@ -127,6 +127,24 @@ int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const d
                        const double* alpha_host, int64_t N, double* u_host, void* workspace,
                        size_t ws_bytes, fgt1d_stream stream);
 
+/* Gradients of L = sum_i grad_u[i] u_i for the transform computed by fgt1d_execute
+ * (the SOE operator of eq. 1.3 with the plan's nodes; the paper has no gradients):
+ *   grad_alpha[j] = sum_i grad_u[i] S(x_i - y_j)      (the transform with roles swapped)
+ *   grad_x[i]     = grad_u[i] sum_j alpha_j S'(x_i - y_j)
+ *   grad_y[j]     = -alpha_j sum_i grad_u[i] S'(x_i - y_j)
+ *   grad_delta[0] = sum_ij grad_u[i] alpha_j dS(x_i - y_j; delta)/d delta
+ * with S' taken as 0 at coincident points (S has a cusp there).  Each sum runs on the
+ * same sorted recurrences as the transform (eqs. 4.5-4.6) with a second evaluation
+ * channel Re sum_k V_k (h+ - h-), V_k = -tau_k W_k / sqrt(delta); grad_delta uses the
+ * scale invariance sum x dL/dx + sum y dL/dy + 2 delta dL/ddelta = 0.  Device arrays:
+ * grad_u[M]; outputs grad_x[M], grad_y[N], grad_alpha[N], grad_delta[1], any of which
+ * may be NULL (not computed).  Workspace from fgt1d_backward_workspace_size.
+ * Stream-ordered like fgt1d_execute. */
+int fgt1d_backward_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes);
+int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y, const double* alpha,
+                   int64_t N, const double* grad_u, double* grad_x, double* grad_y, double* grad_alpha,
+                   double* grad_delta, void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
 /* Steps a1-a2 alone (Sec. 4, first step; Sec. 5 sorting): the stable sort of the
  * merged points.  perm[p] (device, uint32, length M + N) receives the merged index at
  * sorted position p.  Workspace from fgt1d_sort_workspace_size. */

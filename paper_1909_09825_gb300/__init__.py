@@ -7,4 +7,5 @@ and the sorted forward/backward recurrences of Sec. 4.  Every step runs in the
 CUDA library libfgt1d.so (C ABI in include/fgt1d.h); this package only marshals
 arguments.  Import is lazy: the library is loaded on first use.
 """
-from .fgt1d import Plan, soe_cf, transform, sort_merged, execute_host, Workspace  # noqa: F401
+from .fgt1d import (Plan, soe_cf, transform, sort_merged, execute_host, Workspace, backward,  # noqa: F401
+                    GaussTransform, gauss_transform)

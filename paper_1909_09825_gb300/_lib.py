@@ -37,6 +37,8 @@ SIGNATURES = {
     "fgt1d_execute_profiled": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P, _P]),
     "fgt1d_workspace_size_host": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_execute_host": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "fgt1d_backward_workspace_size": (_I, [_P, _I64, _I64, _P]),
+    "fgt1d_backward": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "fgt1d_sort_workspace_size": (_I, [_I64, _I64, _P]),
     "fgt1d_sort_merged": (_I, [_P, _I64, _P, _I64, _P, _P, _SZ, _P]),
     "fgt1d_check": (_I, [_P, _SZ, _P]),

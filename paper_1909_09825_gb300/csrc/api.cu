@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, workspace layout, launch sequence.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -21,15 +22,16 @@ struct Layout {
     size_t zero_end = 0;
     size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0;
     size_t hx = 0, hy = 0, ha = 0, hu = 0;
+    size_t fwd2 = 0, gD = 0, gA = 0, gx = 0, gy = 0, parts = 0;   // gradients
     size_t total = 0;
     int64_t sort_tiles = 0, sweep_tiles = 0;
 };
 
-Layout make_layout(int64_t M, int64_t N, int n_e, unsigned flags, bool sweeps, bool host) {
+Layout make_layout(int64_t M, int64_t N, int n_e, unsigned flags, bool sweeps, bool host, bool grad = false) {
     Layout L;
     const int64_t P = M + N;
     L.sort_tiles = (P + kSortTile - 1) / kSortTile;
-    const int tile = (flags & FGT1D_FP32) ? sweep_tile_f32() : sweep_tile_f64();
+    const int tile = std::min(sweep_tile_f32(), sweep_tile_f64());  // descriptors for either tile shape
     L.sweep_tiles = sweeps ? (P + tile - 1) / tile : 0;
     size_t off = 0;
     L.header = off; off += align_up(256);
@@ -46,6 +48,15 @@ Layout make_layout(int64_t M, int64_t N, int n_e, unsigned flags, bool sweeps, b
     if (sweeps) {
         if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * (size_t)P); }
         L.fwd = off; off += align_up(sizeof(double) * (size_t)P);
+    }
+    if (grad) {
+        const size_t mx = (size_t)std::max(M, N);
+        L.fwd2 = off; off += align_up(sizeof(double) * (size_t)P);
+        L.gD = off; off += align_up(sizeof(double) * mx);
+        L.gA = off; off += align_up(sizeof(double) * mx);
+        L.gx = off; off += align_up(sizeof(double) * (size_t)M);
+        L.gy = off; off += align_up(sizeof(double) * (size_t)N);
+        L.parts = off; off += align_up(sizeof(double) * kGradPartials);
     }
     if (host) {
         L.hx = off; off += align_up(sizeof(double) * (size_t)M);
@@ -99,6 +110,9 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
         c.tau_im[k] = p.tau_im[k];
         c.w_re[k] = p.w_re[k];
         c.w_im[k] = p.w_im[k];
+        // V_k = -tau_k s W_k
+        c.v_re[k] = -c.s * (p.tau_re[k] * p.w_re[k] - p.tau_im[k] * p.w_im[k]);
+        c.v_im[k] = -c.s * (p.tau_re[k] * p.w_im[k] + p.tau_im[k] * p.w_re[k]);
         c.tauf_re[k] = (float)p.tau_re[k];
         c.tauf_im[k] = (float)p.tau_im[k];
         // (-tau)^j / j!
@@ -142,11 +156,13 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
 
-int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
-                  double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* ev = nullptr) {
-    auto rec = [&](int i) { return (ev && ev[i]) ? cudaEventRecord(ev[i], st) : cudaSuccess; };
-    if (M == 0) return FGT1D_OK;
-    if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
+// Sort + sweeps for targets x[M], sources y[N] with strengths alpha.  ev selects the
+// evaluation channels (1: values into u, 2: derivative into out2); coinc (may be null)
+// receives the per-target sums of coincident source strengths.
+int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                 double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L, cudaStream_t st,
+                 cudaEvent_t const* evs = nullptr) {
+    auto rec = [&](int i) { return (evs && evs[i]) ? cudaEventRecord(evs[i], st) : cudaSuccess; };
     cudaError_t e = rec(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
     if (e != cudaSuccess) return FGT1D_ECUDA;
@@ -165,17 +181,35 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
     w.alpha = alpha;
     w.mult = L.mult ? reinterpret_cast<double2*>(ws + L.mult) : nullptr;
     w.fwd = ws + L.fwd;
+    w.fwd2 = L.fwd2 ? ws + L.fwd2 : nullptr;
     w.u = u;
+    w.out2 = out2;
     w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
     w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
     w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
     w.status = sa.status;
-    w.tiles = L.sweep_tiles;
+    const bool f32 = (p.flags & FGT1D_FP32) != 0;
+    const int tile = f32 ? sweep_tile_f32() : sweep_tile_f64();
+    w.tiles = (w.P + tile - 1) / tile;
     SweepConsts c = make_consts(p);
-    cudaEvent_t mid = ev ? ev[2] : nullptr;
-    e = (p.flags & FGT1D_FP32) ? launch_sweeps_f32(w, c, st, mid) : launch_sweeps_f64(w, c, st, mid);
+    cudaEvent_t mid = evs ? evs[2] : nullptr;
+    e = f32 ? launch_sweeps_f32(w, c, st, mid, ev) : launch_sweeps_f64(w, c, st, mid, ev);
     if (e == cudaSuccess) e = rec(3);
+    if (e == cudaSuccess && coinc) {
+        e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
+        w.u = coinc;
+        w.tiles = (w.P + sweep_tile_f64() - 1) / sweep_tile_f64();
+        if (e == cudaSuccess) e = launch_coincidence(w, c, st);
+    }
     return cuda_status(e);
+}
+
+int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                  double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr) {
+    if (M == 0) return FGT1D_OK;
+    if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
+    return run_pipeline(p, x, M, y, alpha, N, u, nullptr, 1, nullptr, ws, L, st, evs);
 }
 
 }  // namespace
@@ -228,6 +262,62 @@ extern "C" int fgt1d_execute_profiled(fgt1d_plan plan, const double* x, int64_t 
     }
     return run_transform(*plan, x, M, y, alpha, N, u, static_cast<char*>(workspace), L,
                          static_cast<cudaStream_t>(stream), reinterpret_cast<cudaEvent_t const*>(events));
+}
+
+extern "C" int fgt1d_backward_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
+    if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, false, true).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y, const double* alpha,
+                              int64_t N, const double* grad_u, double* grad_x, double* grad_y, double* grad_alpha,
+                              double* grad_delta, void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    if ((M > 0 && (!x || !grad_u)) || (N > 0 && (!y || !alpha))) return FGT1D_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0 || N == 0) {  // no pair interacts: every gradient is zero
+        cudaError_t e = cudaSuccess;
+        if (grad_x && M) e = cudaMemsetAsync(grad_x, 0, sizeof(double) * (size_t)M, st);
+        if (e == cudaSuccess && grad_y && N) e = cudaMemsetAsync(grad_y, 0, sizeof(double) * (size_t)N, st);
+        if (e == cudaSuccess && grad_alpha && N) e = cudaMemsetAsync(grad_alpha, 0, sizeof(double) * (size_t)N, st);
+        if (e == cudaSuccess && grad_delta) e = cudaMemsetAsync(grad_delta, 0, sizeof(double), st);
+        return cuda_status(e);
+    }
+    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false, true);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    char* ws = static_cast<char*>(workspace);
+    double sumV = 0.0;
+    {
+        SweepConsts c = make_consts(*plan);
+        for (int k = 0; k < plan->n_e; ++k) sumV += c.v_re[k];
+    }
+    double* D = reinterpret_cast<double*>(ws + L.gD);
+    double* A = reinterpret_cast<double*>(ws + L.gA);
+    double* gx = grad_x ? grad_x : reinterpret_cast<double*>(ws + L.gx);
+    double* gy = grad_y ? grad_y : reinterpret_cast<double*>(ws + L.gy);
+    const bool need_x = grad_x || grad_delta, need_y = grad_y || grad_delta, need_a = grad_alpha != nullptr;
+    if (need_x) {
+        // targets x, sources y, strengths alpha: D_i = Re sum V (h+ - h-), A_i coincident sums
+        r = run_pipeline(*plan, x, M, y, alpha, N, nullptr, D, 2, A, ws, L, st);
+        if (r) return r;
+        if (launch_grad_assemble(grad_u, D, A, sumV, M, gx, st) != cudaSuccess) return FGT1D_ECUDA;
+    }
+    if (need_a || need_y) {
+        // targets y, sources x, strengths grad_u: values -> dL/dalpha, derivative -> dL/dy / alpha
+        const int ev = (need_a ? 1 : 0) | (need_y ? 2 : 0);
+        r = run_pipeline(*plan, y, N, x, grad_u, M, grad_alpha, need_y ? D : nullptr, ev, need_y ? A : nullptr, ws, L,
+                         st);
+        if (r) return r;
+        if (need_y && launch_grad_assemble(alpha, D, A, sumV, N, gy, st) != cudaSuccess) return FGT1D_ECUDA;
+    }
+    if (grad_delta) {
+        if (launch_grad_delta(x, gx, M, y, gy, N, plan->delta, reinterpret_cast<double*>(ws + L.parts), kGradPartials,
+                              grad_delta, st) != cudaSuccess)
+            return FGT1D_ECUDA;
+    }
+    return FGT1D_OK;
 }
 
 extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,

@@ -34,6 +34,7 @@ struct SweepConsts {
     float s_f;                      // the same in FP32
     double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
     double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
+    double v_re[FGT1D_MAX_TERMS], v_im[FGT1D_MAX_TERMS];   // V_k = -tau_k s W_k (derivative weights)
     // Taylor coefficients (-tau_k)^j / j!, j = 0..kTaylorMax, per term
     double tc_re[FGT1D_MAX_TERMS][kTaylorMax + 1], tc_im[FGT1D_MAX_TERMS][kTaylorMax + 1];
     float tcf_re[FGT1D_MAX_TERMS][kTaylorMax + 1], tcf_im[FGT1D_MAX_TERMS][kTaylorMax + 1];

@@ -61,7 +61,9 @@ struct SweepArgs {
     const double* alpha;
     double2* mult;          // [n_e][P] multiplier table (FP64 path) or nullptr
     void* fwd;              // [P] forward partial sums Re sum_k W_k h+_k at targets (double; float on the FP32 path)
-    double* u;              // [M] output
+    void* fwd2;             // [P] forward partial sums Re sum_k V_k h+_k (derivative channel)
+    double* u;              // [M] output: Re sum_k W_k (h+ + h-) (value channel)
+    double* out2;           // [M] output: Re sum_k V_k (h+ - h-) (derivative channel)
     TileDesc* fdesc;        // [tiles][n_e]
     TileDesc* bdesc;        // [tiles][n_e]
     uint32_t* tile_ctr;     // [2]
@@ -71,11 +73,24 @@ struct SweepArgs {
 
 int sweep_tile_f64();  // points per sweep tile
 int sweep_tile_f32();
+// Evaluation channels of the sweeps: bit 0 values Re sum W (h+ + h-) into u, bit 1 the
+// derivative Re sum V (h+ - h-) into out2 (V_k = -tau_k s W_k).
 // `mid` (may be null) is recorded on st between the forward and the backward kernel.
-cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
-cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
+cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
+cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
+// Coincidence sums: u[i] = sum of alpha over the sources at exactly the coordinate of
+// target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).
+cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
 
 // copies the sorted merged indices (final sort buffer) to perm
 cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st);
+
+// gradient assembly: out[i] = w[i] (D[i] - A[i] sumV)
+cudaError_t launch_grad_assemble(const double* w, const double* D, const double* A, double sumV, int64_t n,
+                                 double* out, cudaStream_t st);
+// *out = -(1/(2 delta)) (sum (x - x[0]) gx + sum (y - x[0]) gy), with nb partial sums
+constexpr int kGradPartials = 608;
+cudaError_t launch_grad_delta(const double* x, const double* gx, int64_t M, const double* y, const double* gy,
+                              int64_t N, double delta, double* partials, int nb, double* out, cudaStream_t st);
 
 }  // namespace fgt1d

@@ -442,7 +442,10 @@ __device__ __forceinline__ double real_to_f64<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ double real_to_f64<float>(float v) { return f32_to_f64(v); }
 
-template <typename Real, int NE, int T, int R>
+// EV: evaluation channels (bit 0 values, bit 1 derivative).  CO: coincidence mode
+// (NE = 1, multiplier 1 on zero gaps and 0 otherwise, unit weight; the per-target sums
+// are written straight to a.u), used by the gradients.
+template <typename Real, int NE, int T, int R, int EV, bool CO>
 __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepConsts c) {
     using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
@@ -503,7 +506,12 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     if (tid >= T - NE && tile > 0) {
         const int k = tid - (T - NE);
         double mr, mi;
-        cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (zend - zprev), mr, mi);
+        if constexpr (CO) {
+            mr = zend == zprev ? 1.0 : 0.0;
+            mi = 0.0;
+        } else {
+            cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (zend - zprev), mr, mi);
+        }
         s_M[k][0] = mr;
         s_M[k][1] = mi;
     }
@@ -511,22 +519,30 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     // phase A: per term, thread aggregates and the warp scan
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
-        const int deg = taylor_degree<Real>(c, k, hw);
-        double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
         Real fr = 0, fi = 0;
-        with_degree<Real>(deg, [&](auto Dc) {
-#pragma unroll 4
-            for (int r = 0; r < R; ++r) {
-                Real mr, mi;
-                taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
-                if constexpr (kF64) {
-                    if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
-                }
-                cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-            }
-        });
         Real Mr, Mi;
-        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+        if constexpr (CO) {
+#pragma unroll 4
+            for (int r = 0; r < R; ++r)
+                fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
+            Mr = thsp == Real(0) ? Real(1) : Real(0);
+            Mi = 0;
+        } else {
+            const int deg = taylor_degree<Real>(c, k, hw);
+            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
+            with_degree<Real>(deg, [&](auto Dc) {
+#pragma unroll 4
+                for (int r = 0; r < R; ++r) {
+                    Real mr, mi;
+                    taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
+                    if constexpr (kF64) {
+                        if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
+                    }
+                    cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+                }
+            });
+            multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Real Mor = __shfl_up_sync(0xffffffffu, Mr, o), Moi = __shfl_up_sync(0xffffffffu, Mi, o);
@@ -552,10 +568,18 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         tile_combine<NE, NW>(a, a.fdesc, tile, -1, tile == 0, tile > 0 ? s_M[k][0] : 1.0, tile > 0 ? s_M[k][1] : 0.0,
                              s_w, s_win, k);
     __syncthreads();
-    // phase C: apply the carries, final pass, evaluation at targets
+    // phase C: apply the carries, final pass, evaluation at targets.  The value channel
+    // accumulates in registers, the derivative channel in shared memory (over the
+    // coordinates / gaps, which the FP64 path no longer needs and the FP32 path keeps
+    // in the first half of the region).
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
+    Real* s_acc2 = kF64 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    if constexpr ((EV & 2) != 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
+    }
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
         const Real* sc = s_scan + (size_t)k * 4 * T;
@@ -563,13 +587,31 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
                    sc[2 * T + tid], sc[3 * T + tid], fr, fi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        if constexpr (kF64) {
+        const Real Vr = (Real)c.v_re[k], Vi = (Real)c.v_im[k];
+        auto eval = [&](int r) {
+            if ((tmask >> r) & 1u) {
+                if constexpr (CO) {
+                    acc[r] += fr;
+                } else {
+                    if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+                    if constexpr ((EV & 2) != 0)
+                        s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+                }
+            }
+        };
+        if constexpr (CO) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
+                eval(r);
+            }
+        } else if constexpr (kF64) {
             const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
                 cfma<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-                if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+                eval(r);
             }
         } else {
             with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
@@ -578,30 +620,28 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                     Real mr, mi;
                     taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
                     cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-                    if ((tmask >> r) & 1u) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
+                    eval(r);
                 }
             });
         }
     }
-    // forward partial sums, written coalesced through shared memory
+    // outputs, written coalesced through shared memory (values staged over s_al)
     __syncthreads();
-    if constexpr (kF64) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = acc[r];
-        __syncthreads();
-        double* __restrict__ fwd = static_cast<double*>(a.fwd);
-        for (int i = tid; i < nvalid; i += T) fwd[base + i] = s_z[pad<R>(i)];
+    for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
+    __syncthreads();
+    if constexpr (CO) {
+        for (int i = tid; i < nvalid; i += T)
+            if ((s_tgt[i >> 5] >> (i & 31)) & 1u) a.u[(int64_t)vals[base + i] - a.N] = real_to_f64<Real>(s_al[pad<R>(i)]);
     } else {
-        float* s_o = reinterpret_cast<float*>(s_z);
-#pragma unroll
-        for (int r = 0; r < R; ++r) s_o[pad<R>(i0 + r)] = acc[r];
-        __syncthreads();
-        float* __restrict__ fwd = static_cast<float*>(a.fwd);
-        for (int i = tid; i < nvalid; i += T) fwd[base + i] = s_o[pad<R>(i)];
+        for (int i = tid; i < nvalid; i += T) {
+            if constexpr ((EV & 1) != 0) static_cast<Real*>(a.fwd)[base + i] = s_al[pad<R>(i)];
+            if constexpr ((EV & 2) != 0) static_cast<Real*>(a.fwd2)[base + i] = s_acc2[pad<R>(i)];
+        }
     }
 }
 
-template <typename Real, int NE, int T, int R>
+template <typename Real, int NE, int T, int R, int EV>
 __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepConsts c) {
     using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
@@ -726,6 +766,11 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
+    Real* s_acc2 = kF64 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    if constexpr ((EV & 2) != 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
+    }
 #pragma unroll 1
     for (int k = 0; k < NE; ++k) {
         const Real* sc = s_scan + (size_t)k * 4 * T;
@@ -733,6 +778,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
                    sc[2 * T + tid], sc[3 * T + tid], br, bi);
         const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
+        const Real Vr = (Real)c.v_re[k], Vi = (Real)c.v_im[k];
         const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
         with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll
@@ -740,31 +786,28 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                 Real mr, mi;
                 mult_at(k, Dc, r, mr, mi);
                 cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
-                if ((tmask >> r) & 1u) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+                if ((tmask >> r) & 1u) {
+                    if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+                    if constexpr ((EV & 2) != 0)
+                        s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                }
             }
         });
     }
     __syncthreads();
-    if constexpr (kF64) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) s_z[pad<R>(i0 + r)] = acc[r];
-    } else {
-        float* s_o = reinterpret_cast<float*>(s_z);
-#pragma unroll
-        for (int r = 0; r < R; ++r) s_o[pad<R>(i0 + r)] = acc[r];
-    }
+    for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
     __syncthreads();
     for (int i = tid; i < nvalid; i += T) {
         if ((s_tgt[i >> 5] >> (i & 31)) & 1u) {
             const int64_t p = base + i;
-            const uint32_t v = vals[p];
-            double out;
-            if constexpr (kF64) {
-                out = static_cast<const double*>(a.fwd)[p] + s_z[pad<R>(i)];
-            } else {
-                out = f32_to_f64(static_cast<const float*>(a.fwd)[p] + reinterpret_cast<float*>(s_z)[pad<R>(i)]);
-            }
-            a.u[(int64_t)v - a.N] = out;
+            const int64_t t = (int64_t)vals[p] - a.N;
+            if constexpr ((EV & 1) != 0)
+                a.u[t] = kF64 ? (double)(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)])
+                              : real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
+            if constexpr ((EV & 2) != 0)
+                a.out2[t] = kF64 ? (double)(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)])
+                                 : real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
         }
     }
 }

@@ -1,41 +1,13 @@
-// FP32 instantiations of the sweep kernels (tile = 256 threads x 16 points).
-#include "sweep.cuh"
+// FP32 sweeps for the transform (value channel).
+#include "sweep_launch.cuh"
 
 namespace fgt1d {
 
-namespace {
-constexpr int kT = 256, kR = 16;
+int sweep_tile_f32() { return kT32 * kR32; }
 
-template <int NE>
-cudaError_t run(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {
-    const size_t smem = SweepSmem<float, NE, kT, kR>::bytes;
-    auto kf = k_sweep_fwd<float, NE, kT, kR>;
-    auto kb = k_sweep_bwd<float, NE, kT, kR>;
-    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kf<<<(unsigned)a.tiles, kT, smem, st>>>(a, c);
-    if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
-    kb<<<(unsigned)a.tiles, kT, smem, st>>>(a, c);
-    return cudaGetLastError();
-}
-}  // namespace
-
-int sweep_tile_f32() { return kT * kR; }
-
-cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {
-    switch (c.n_e) {
-        case 1: return run<1>(a, c, st, mid);
-        case 2: return run<2>(a, c, st, mid);
-        case 3: return run<3>(a, c, st, mid);
-        case 4: return run<4>(a, c, st, mid);
-        case 5: return run<5>(a, c, st, mid);
-        case 6: return run<6>(a, c, st, mid);
-        case 7: return run<7>(a, c, st, mid);
-        case 8: return run<8>(a, c, st, mid);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev) {
+    if (ev == 1) return run_sweeps_ne<float, kT32, kR32, 1>(a, c, st, mid);
+    return launch_sweeps_f32_ev(a, c, st, mid, ev);
 }
 
 }  // namespace fgt1d

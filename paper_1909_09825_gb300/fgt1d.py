@@ -169,3 +169,63 @@ def sort_merged(x, y, workspace=None, stream=None):
           "sort_merged")
     check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "sort_merged (device)")
     return perm.to(torch.int64) & 0xFFFFFFFF
+
+
+def backward(plan, x, y, alpha, grad_u, want=(True, True, True, True), workspace=None, stream=None,
+             sync_check=True):
+    """Gradients of L = sum_i grad_u[i] u_i: returns (grad_x, grad_y, grad_alpha, grad_delta),
+    each None where `want` is False (order: x, y, alpha, delta)."""
+    for t, n in ((x, "x"), (y, "y"), (alpha, "alpha"), (grad_u, "grad_u")):
+        _dev(t, n)
+    M, N = x.numel(), y.numel()
+    dev = x.device
+    gx = torch.empty(M, dtype=torch.float64, device=dev) if want[0] else None
+    gy = torch.empty(N, dtype=torch.float64, device=dev) if want[1] else None
+    ga = torch.empty(N, dtype=torch.float64, device=dev) if want[2] else None
+    gd = torch.empty(1, dtype=torch.float64, device=dev) if want[3] else None
+    b = ctypes.c_size_t()
+    check(lib().fgt1d_backward_workspace_size(plan.handle, M, N, ctypes.byref(b)), "backward_workspace_size")
+    ws = _workspace(workspace, dev, b.value)
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = _stream_ptr(stream)
+    check(lib().fgt1d_backward(plan.handle, p(x), M, p(y), p(alpha), N, p(grad_u), p(gx), p(gy), p(ga), p(gd),
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "backward")
+    if sync_check:
+        check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "backward (device)")
+    return gx, gy, ga, gd
+
+
+class GaussTransform(torch.autograd.Function):
+    """u = FGT(x, y, alpha; delta) with a hand-written adjoint (fgt1d_backward)."""
+
+    @staticmethod
+    def forward(ctx, x, y, alpha, delta, plan):
+        u = transform(plan, x.contiguous(), y.contiguous(), alpha.contiguous())
+        ctx.save_for_backward(x, y, alpha)
+        ctx.plan = plan
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        x, y, alpha = ctx.saved_tensors
+        need = ctx.needs_input_grad
+        gx, gy, ga, gd = backward(ctx.plan, x.contiguous(), y.contiguous(), alpha.contiguous(), gu.contiguous(),
+                                  want=(need[0], need[1], need[2], need[3]))
+        if gd is not None:
+            gd = gd.reshape(())
+        return gx, gy, ga, gd, None
+
+
+_plans = {}
+
+
+def gauss_transform(x, y, alpha, delta, eps=1e-10, precision="fp64"):
+    """Differentiable u_i = sum_j exp(-(x_i - y_j)^2 / (4 delta)) alpha_j.  delta may be a
+    float or a 0-dim float64 tensor (on any device) that requires grad."""
+    d = float(delta.detach().cpu()) if isinstance(delta, torch.Tensor) else float(delta)
+    key = (d, float(eps), precision)
+    plan = _plans.get(key)
+    if plan is None:
+        plan = _plans[key] = Plan(d, eps, precision=precision)
+    dt = delta if isinstance(delta, torch.Tensor) else torch.tensor(d, dtype=torch.float64)
+    return GaussTransform.apply(x, y, alpha, dt, plan)

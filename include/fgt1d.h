@@ -57,6 +57,7 @@ typedef void* fgt1d_stream;              /* a cudaStream_t */
 #define FGT1D_ETIMEOUT 5      /* a bounded inter-block wait gave up (found on the device) */
 #define FGT1D_ECUDA 6         /* a CUDA runtime call failed */
 #define FGT1D_EWORKSPACE 7    /* workspace NULL, misaligned or smaller than required */
+#define FGT1D_ETOOLARGE 8     /* problem larger than the fixed scratch of fgt1d_execute_noalloc */
 
 /* plan flags */
 #define FGT1D_FP64 0u         /* every step in FP64 */
@@ -126,6 +127,18 @@ int fgt1d_workspace_size_host(fgt1d_plan plan, int64_t M, int64_t N, size_t* byt
 int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
                        const double* alpha_host, int64_t N, double* u_host, void* workspace,
                        size_t ws_bytes, fgt1d_stream stream);
+
+/* The transform of fgt1d_execute for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Takes only the inputs and the output: its scratch is a
+ * fixed 16 MiB array in the library's device memory, held on every GPU that loads the
+ * library until the process exits, which fits any plan with M + N <= 65,536 points;
+ * more points return FGT1D_ETOOLARGE.  The first call on a device looks up the
+ * array's address (once per device, that device current): make it before any stream
+ * capture.  All calls share the array, so calls whose GPU work can overlap race and
+ * must be ordered by the caller.  Device-side conditions (NaN/Inf coordinates, an
+ * expired wait) are not reported by this entry point. */
+int fgt1d_execute_noalloc(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                          const double* alpha, int64_t N, double* u, fgt1d_stream stream);
 
 /* Gradients of L = sum_i grad_u[i] u_i for the transform computed by fgt1d_execute
  * (the SOE operator of eq. 1.3 with the plan's nodes; the paper has no gradients):

@@ -17,6 +17,7 @@ FGT1D_ENOMEM = 4
 FGT1D_ETIMEOUT = 5
 FGT1D_ECUDA = 6
 FGT1D_EWORKSPACE = 7
+FGT1D_ETOOLARGE = 8
 FGT1D_FP64 = 0
 FGT1D_FP32 = 1
 MAX_TERMS = 8
@@ -37,6 +38,7 @@ SIGNATURES = {
     "fgt1d_execute_profiled": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P, _P]),
     "fgt1d_workspace_size_host": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_execute_host": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "fgt1d_execute_noalloc": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P]),
     "fgt1d_backward_workspace_size": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_backward": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "fgt1d_sort_workspace_size": (_I, [_I64, _I64, _P]),

@@ -213,6 +213,22 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
 }
 
 }  // namespace
+
+int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,
+                     int64_t N, double* u, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!sizes_ok(M, N)) return FGT1D_EINVAL;
+    Layout L = make_layout(M, N, p.n_e, p.flags, true, false);
+    if (M > 0 && N > 0) {
+        int r = ws_ok(ws, ws_bytes, L);
+        if (r) return r;
+    }
+    return run_transform(p, x, M, y, alpha, N, u, static_cast<char*>(ws), L, st);
+}
+
+size_t transform_workspace_bytes(const fgt1d_plan_s& p, int64_t M, int64_t N) {
+    return make_layout(M, N, p.n_e, p.flags, true, false).total;
+}
+
 }  // namespace fgt1d
 
 using namespace fgt1d;
@@ -389,6 +405,7 @@ extern "C" const char* fgt1d_strerror(int status) {
         case FGT1D_ETIMEOUT: return "a bounded inter-block wait expired";
         case FGT1D_ECUDA: return "CUDA runtime error";
         case FGT1D_EWORKSPACE: return "workspace missing, misaligned or too small";
+        case FGT1D_ETOOLARGE: return "problem larger than the library's fixed scratch";
         default: return "unknown status";
     }
 }

@@ -85,6 +85,11 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
 // copies the sorted merged indices (final sort buffer) to perm
 cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st);
 
+// fgt1d_execute on a caller-given workspace (checked against the layout size)
+int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,
+                     int64_t N, double* u, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t transform_workspace_bytes(const fgt1d_plan_s& p, int64_t M, int64_t N);
+
 // gradient assembly: out[i] = w[i] (D[i] - A[i] sumV)
 cudaError_t launch_grad_assemble(const double* w, const double* D, const double* A, double sumV, int64_t n,
                                  double* out, cudaStream_t st);

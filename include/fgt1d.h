@@ -29,8 +29,8 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute entry
  *    points are asynchronous: they enqueue work and return.  Argument errors are
  *    returned immediately; conditions found on the device (a NaN/Inf coordinate,
- *    an expired bounded wait) are recorded in the workspace and returned by
- *    fgt1d_check, which synchronises the stream.
+ *    an expired bounded wait, a bad batch item) are recorded in the workspace and
+ *    returned by fgt1d_check, which synchronises the stream.
  *  - Return value: FGT1D_OK (0) or one of the FGT1D_E* codes below.
  *  - P = M + N must be below 2^31.  M = 0 is a no-op; N = 0 writes u = 0.
  */
@@ -128,6 +128,25 @@ int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const d
                        const double* alpha_host, int64_t N, double* u_host, void* workspace,
                        size_t ws_bytes, fgt1d_stream stream);
 
+/* A batch of B independent transforms of uneven sizes and bandwidths in one pass of
+ * the same kernels (the same method per item; the paper treats one transform).  Item b
+ * has targets x[x_off[b] .. x_off[b+1]), sources y and strengths alpha at
+ * [y_off[b] .. y_off[b+1]), bandwidth delta[b] (device array of B values, or NULL for
+ * the plan's delta; the plan fixes eps and thus n_e), and writes u[x_off[b] ..
+ * x_off[b+1]).  x_off and y_off are DEVICE arrays of B + 1 non-decreasing offsets in
+ * [0, M_total] and [0, N_total]; they are read on the device, so the call can be captured
+ * in a CUDA graph and replayed with new offsets, bandwidths and data.  Every item's
+ * merged points are padded to whole 4096-point tiles; the workspace
+ * (fgt1d_batched_workspace_size, an upper bound for any offsets with these totals)
+ * therefore grows by at most one tile per item.  An item with bad offsets or a delta
+ * that is not positive and finite is skipped and reported by fgt1d_check as
+ * FGT1D_EINVAL.  Requires (M_total + N_total) / 4096 + B < 2^19. */
+int fgt1d_batched_workspace_size(fgt1d_plan plan, int B, int64_t M_total, int64_t N_total, size_t* bytes);
+int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off,
+                          const double* delta, const double* x, int64_t M_total, const double* y,
+                          const double* alpha, int64_t N_total, double* u, void* workspace, size_t ws_bytes,
+                          fgt1d_stream stream);
+
 /* The transform of fgt1d_execute for callers that cannot allocate device memory (no
  * counterpart in the paper).  Takes only the inputs and the output: its scratch is a
  * fixed 16 MiB array in the library's device memory, held on every GPU that loads the
@@ -166,8 +185,8 @@ int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, ui
                       void* workspace, size_t ws_bytes, fgt1d_stream stream);
 
 /* Synchronises `stream`, then returns and clears the device status recorded in the
- * workspace by the previous compute calls: FGT1D_OK, FGT1D_ENONFINITE, FGT1D_ETIMEOUT,
- * or FGT1D_ECUDA if the stream reported an error. */
+ * workspace by the previous compute calls: FGT1D_OK, FGT1D_EINVAL (a bad batch item),
+ * FGT1D_ENONFINITE, FGT1D_ETIMEOUT, or FGT1D_ECUDA if the stream reported an error. */
 int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream);
 
 /* Human-readable text of a status code (static storage). */

@@ -39,6 +39,8 @@ SIGNATURES = {
     "fgt1d_workspace_size_host": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_execute_host": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
     "fgt1d_execute_noalloc": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P]),
+    "fgt1d_batched_workspace_size": (_I, [_P, _I, _I64, _I64, _P]),
+    "fgt1d_execute_batched": (_I, [_P, _I, _P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
     "fgt1d_backward_workspace_size": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_backward": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "fgt1d_sort_workspace_size": (_I, [_I64, _I64, _P]),

@@ -14,44 +14,51 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace layout.  [0, zero_end) is cleared at the start of every call.
+// Workspace layout.  [0, zero_end) is cleared at the start of every pipeline.  Sizes are
+// upper bounds for B items totalling M targets and N sources: each item pads its merged
+// range to whole tiles, which adds at most one tile per item.
 struct Layout {
-    size_t header = 0;       // status (u32 at 0), sort tile counters (8 u32 at 32),
-                             // sweep tile counters (2 u32 at 64), SortPlan at 128
+    size_t header = 0;       // status (u32 at 0), sort tile counters (8 u32 at 32), sweep tile
+                             // counters (2 u32 at 64), total tiles (i64 at 80), SortPlan at 128
     size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;
     size_t zero_end = 0;
-    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0;
-    size_t hx = 0, hy = 0, ha = 0, hu = 0;
-    size_t fwd2 = 0, gD = 0, gA = 0, gx = 0, gy = 0, parts = 0;   // gradients
+    size_t items = 0;
+    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0, fwd2 = 0;
+    size_t gD = 0, gA = 0, gx = 0, gy = 0, parts = 0;   // gradients
+    size_t hx = 0, hy = 0, ha = 0, hu = 0;              // device copies of host arrays
     size_t total = 0;
-    int64_t sort_tiles = 0, sweep_tiles = 0;
+    int64_t max_tiles = 0, Ppad = 0;
+    int B = 1;
 };
 
-Layout make_layout(int64_t M, int64_t N, int n_e, unsigned flags, bool sweeps, bool host, bool grad = false) {
+Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sweeps, bool host, bool grad = false) {
     Layout L;
+    L.B = B;
     const int64_t P = M + N;
-    L.sort_tiles = (P + kSortTile - 1) / kSortTile;
-    const int tile = std::min(sweep_tile_f32(), sweep_tile_f64());  // descriptors for either tile shape
-    L.sweep_tiles = sweeps ? (P + tile - 1) / tile : 0;
+    L.max_tiles = (P + kTile - 1) / kTile + (B - 1);
+    L.Ppad = L.max_tiles * kTile;
+    const size_t Pp = (size_t)L.Ppad;
     size_t off = 0;
     L.header = off; off += align_up(256);
-    L.hist = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256);
-    L.offs = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256);
-    L.sort_desc = off; off += align_up(sizeof(uint64_t) * kSortDigits * (size_t)L.sort_tiles * 256);
-    L.fdesc = off; off += align_up(sizeof(TileDesc) * (size_t)L.sweep_tiles * (size_t)n_e);
-    L.bdesc = off; off += align_up(sizeof(TileDesc) * (size_t)L.sweep_tiles * (size_t)n_e);
+    L.hist = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256 * (size_t)B);
+    L.offs = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256 * (size_t)B);
+    L.sort_desc = off; off += align_up(sizeof(uint64_t) * kSortDigits * (size_t)L.max_tiles * 256);
+    const int64_t st = sweeps ? L.max_tiles : 0;
+    L.fdesc = off; off += align_up(sizeof(TileDesc) * (size_t)st * (size_t)n_e);
+    L.bdesc = off; off += align_up(sizeof(TileDesc) * (size_t)st * (size_t)n_e);
     L.zero_end = off;
-    L.keysA = off; off += align_up(sizeof(uint64_t) * (size_t)P);
-    L.keysB = off; off += align_up(sizeof(uint64_t) * (size_t)P);
-    L.valsA = off; off += align_up(sizeof(uint32_t) * (size_t)P);
-    L.valsB = off; off += align_up(sizeof(uint32_t) * (size_t)P);
+    L.items = off; off += align_up(sizeof(Item) * (size_t)B);
+    L.keysA = off; off += align_up(sizeof(uint64_t) * Pp);
+    L.keysB = off; off += align_up(sizeof(uint64_t) * Pp);
+    L.valsA = off; off += align_up(sizeof(uint32_t) * Pp);
+    L.valsB = off; off += align_up(sizeof(uint32_t) * Pp);
     if (sweeps) {
-        if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * (size_t)P); }
-        L.fwd = off; off += align_up(sizeof(double) * (size_t)P);
+        if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
+        L.fwd = off; off += align_up(sizeof(double) * Pp);
     }
     if (grad) {
         const size_t mx = (size_t)std::max(M, N);
-        L.fwd2 = off; off += align_up(sizeof(double) * (size_t)P);
+        L.fwd2 = off; off += align_up(sizeof(double) * Pp);
         L.gD = off; off += align_up(sizeof(double) * mx);
         L.gA = off; off += align_up(sizeof(double) * mx);
         L.gx = off; off += align_up(sizeof(double) * (size_t)M);
@@ -77,12 +84,15 @@ int ws_ok(const void* ws, size_t ws_bytes, const Layout& L) {
     return FGT1D_OK;
 }
 
-SortArgs sort_args(const double* x, int64_t M, const double* y, int64_t N, char* ws, const Layout& L) {
+SortArgs sort_args(const double* x, const double* y, int64_t N, char* ws, const Layout& L) {
     SortArgs a;
     a.x = x;
     a.y = y;
     a.N = N;
-    a.P = M + N;
+    a.items = reinterpret_cast<const Item*>(ws + L.items);
+    a.B = L.B;
+    a.total_tiles = reinterpret_cast<const int64_t*>(ws + L.header + 80);
+    a.max_tiles = L.max_tiles;
     a.keysA = reinterpret_cast<uint64_t*>(ws + L.keysA);
     a.keysB = reinterpret_cast<uint64_t*>(ws + L.keysB);
     a.valsA = reinterpret_cast<uint32_t*>(ws + L.valsA);
@@ -91,7 +101,7 @@ SortArgs sort_args(const double* x, int64_t M, const double* y, int64_t N, char*
     a.offs = reinterpret_cast<uint32_t*>(ws + L.offs);
     a.plan = reinterpret_cast<SortPlan*>(ws + L.header + 128);
     a.desc = reinterpret_cast<uint64_t*>(ws + L.sort_desc);
-    a.desc_stride = (size_t)L.sort_tiles * 256;
+    a.desc_stride = (size_t)L.max_tiles * 256;
     a.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 32);
     a.status = reinterpret_cast<uint32_t*>(ws + L.header);
     return a;
@@ -110,9 +120,9 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
         c.tau_im[k] = p.tau_im[k];
         c.w_re[k] = p.w_re[k];
         c.w_im[k] = p.w_im[k];
-        // V_k = -tau_k s W_k
-        c.v_re[k] = -c.s * (p.tau_re[k] * p.w_re[k] - p.tau_im[k] * p.w_im[k]);
-        c.v_im[k] = -c.s * (p.tau_re[k] * p.w_im[k] + p.tau_im[k] * p.w_re[k]);
+        // V'_k = -tau_k W_k (the derivative channel multiplies by s per item)
+        c.v_re[k] = -(p.tau_re[k] * p.w_re[k] - p.tau_im[k] * p.w_im[k]);
+        c.v_im[k] = -(p.tau_re[k] * p.w_im[k] + p.tau_im[k] * p.w_re[k]);
         c.tauf_re[k] = (float)p.tau_re[k];
         c.tauf_im[k] = (float)p.tau_im[k];
         // (-tau)^j / j!
@@ -156,23 +166,43 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
 
+// Where the items come from: one item (M targets, N sources, the plan's delta), or B
+// items from device offsets and optional per-item bandwidths.
+struct ItemSource {
+    int B = 1;
+    const int64_t* x_off = nullptr;
+    const int64_t* y_off = nullptr;
+    const double* delta = nullptr;
+};
+
 // Sort + sweeps for targets x[M], sources y[N] with strengths alpha.  ev selects the
 // evaluation channels (1: values into u, 2: derivative into out2); coinc (may be null)
 // receives the per-target sums of coincident source strengths.
 int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
-                 double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L, cudaStream_t st,
-                 cudaEvent_t const* evs = nullptr) {
+                 const ItemSource& src, double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L,
+                 cudaStream_t st, cudaEvent_t const* evs = nullptr) {
     auto rec = [&](int i) { return (evs && evs[i]) ? cudaEventRecord(evs[i], st) : cudaSuccess; };
     cudaError_t e = rec(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
     if (e != cudaSuccess) return FGT1D_ECUDA;
-    SortArgs sa = sort_args(x, M, y, N, ws, L);
+    Item* items = reinterpret_cast<Item*>(ws + L.items);
+    int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.header);
+    e = src.x_off ? launch_items(src.B, src.x_off, src.y_off, src.delta, p.delta, items, total_tiles, status,
+                                 L.max_tiles, M, N, st)
+                  : launch_item_single(M, N, p.delta, items, total_tiles, st);
+    if (e != cudaSuccess) return FGT1D_ECUDA;
+    SortArgs sa = sort_args(x, y, N, ws, L);
     e = launch_sort(sa, st);
     if (e == cudaSuccess) e = rec(1);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w;
-    w.P = M + N;
     w.N = N;
+    w.items = items;
+    w.B = L.B;
+    w.total_tiles = total_tiles;
+    w.max_tiles = L.max_tiles;
+    w.Ppad = L.Ppad;
     w.keysA = sa.keysA;
     w.keysB = sa.keysB;
     w.valsA = sa.valsA;
@@ -187,10 +217,8 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
     w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
     w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
-    w.status = sa.status;
+    w.status = status;
     const bool f32 = (p.flags & FGT1D_FP32) != 0;
-    const int tile = f32 ? sweep_tile_f32() : sweep_tile_f64();
-    w.tiles = (w.P + tile - 1) / tile;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
     e = f32 ? launch_sweeps_f32(w, c, st, mid, ev) : launch_sweeps_f64(w, c, st, mid, ev);
@@ -199,7 +227,6 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
         w.u = coinc;
-        w.tiles = (w.P + sweep_tile_f64() - 1) / sweep_tile_f64();
         if (e == cudaSuccess) e = launch_coincidence(w, c, st);
     }
     return cuda_status(e);
@@ -209,7 +236,7 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
                   double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr) {
     if (M == 0) return FGT1D_OK;
     if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
-    return run_pipeline(p, x, M, y, alpha, N, u, nullptr, 1, nullptr, ws, L, st, evs);
+    return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, evs);
 }
 
 }  // namespace
@@ -217,7 +244,7 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
 int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,
                      int64_t N, double* u, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (!sizes_ok(M, N)) return FGT1D_EINVAL;
-    Layout L = make_layout(M, N, p.n_e, p.flags, true, false);
+    Layout L = make_layout(M, N, 1, p.n_e, p.flags, true, false);
     if (M > 0 && N > 0) {
         int r = ws_ok(ws, ws_bytes, L);
         if (r) return r;
@@ -226,7 +253,7 @@ int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const do
 }
 
 size_t transform_workspace_bytes(const fgt1d_plan_s& p, int64_t M, int64_t N) {
-    return make_layout(M, N, p.n_e, p.flags, true, false).total;
+    return make_layout(M, N, 1, p.n_e, p.flags, true, false).total;
 }
 
 }  // namespace fgt1d
@@ -235,19 +262,19 @@ using namespace fgt1d;
 
 extern "C" int fgt1d_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
     if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
-    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, false).total;
+    *bytes = make_layout(M, N, 1, plan->n_e, plan->flags, true, false).total;
     return FGT1D_OK;
 }
 
 extern "C" int fgt1d_workspace_size_host(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
     if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
-    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, true).total;
+    *bytes = make_layout(M, N, 1, plan->n_e, plan->flags, true, true).total;
     return FGT1D_OK;
 }
 
 extern "C" int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes) {
     if (!bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
-    *bytes = make_layout(M, N, 1, FGT1D_FP64, false, false).total;
+    *bytes = make_layout(M, N, 1, 1, FGT1D_FP64, false, false).total;
     return FGT1D_OK;
 }
 
@@ -256,7 +283,7 @@ extern "C" int fgt1d_execute(fgt1d_plan plan, const double* x, int64_t M, const 
     if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
     if (M > 0 && (!x || !u)) return FGT1D_EINVAL;
     if (N > 0 && M > 0 && (!y || !alpha)) return FGT1D_EINVAL;
-    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false);
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
     if (M > 0 && N > 0) {
         int r = ws_ok(workspace, ws_bytes, L);
         if (r) return r;
@@ -271,7 +298,7 @@ extern "C" int fgt1d_execute_profiled(fgt1d_plan plan, const double* x, int64_t 
     if (!plan || !sizes_ok(M, N) || !events) return FGT1D_EINVAL;
     if (M > 0 && (!x || !u)) return FGT1D_EINVAL;
     if (N > 0 && M > 0 && (!y || !alpha)) return FGT1D_EINVAL;
-    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false);
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
     if (M > 0 && N > 0) {
         int r = ws_ok(workspace, ws_bytes, L);
         if (r) return r;
@@ -280,9 +307,36 @@ extern "C" int fgt1d_execute_profiled(fgt1d_plan plan, const double* x, int64_t 
                          static_cast<cudaStream_t>(stream), reinterpret_cast<cudaEvent_t const*>(events));
 }
 
+extern "C" int fgt1d_batched_workspace_size(fgt1d_plan plan, int B, int64_t M_total, int64_t N_total,
+                                            size_t* bytes) {
+    if (!plan || !bytes || B < 1 || !sizes_ok(M_total, N_total)) return FGT1D_EINVAL;
+    if ((M_total + N_total + kTile - 1) / kTile + (B - 1) > (int64_t(1) << 31) / kTile) return FGT1D_EINVAL;
+    *bytes = make_layout(M_total, N_total, B, plan->n_e, plan->flags, true, false).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off,
+                                     const double* delta, const double* x, int64_t M_total, const double* y,
+                                     const double* alpha, int64_t N_total, double* u, void* workspace,
+                                     size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || B < 1 || !x_off || !y_off || !sizes_ok(M_total, N_total)) return FGT1D_EINVAL;
+    if ((M_total > 0 && (!x || !u)) || (N_total > 0 && (!y || !alpha))) return FGT1D_EINVAL;
+    if ((M_total + N_total + kTile - 1) / kTile + (B - 1) > (int64_t(1) << 31) / kTile) return FGT1D_EINVAL;
+    Layout L = make_layout(M_total, N_total, B, plan->n_e, plan->flags, true, false);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    ItemSource src;
+    src.B = B;
+    src.x_off = x_off;
+    src.y_off = y_off;
+    src.delta = delta;
+    return run_pipeline(*plan, x, M_total, y, alpha, N_total, src, u, nullptr, 1, nullptr,
+                        static_cast<char*>(workspace), L, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int fgt1d_backward_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
     if (!plan || !bytes || !sizes_ok(M, N)) return FGT1D_EINVAL;
-    *bytes = make_layout(M, N, plan->n_e, plan->flags, true, false, true).total;
+    *bytes = make_layout(M, N, 1, plan->n_e, plan->flags, true, false, true).total;
     return FGT1D_OK;
 }
 
@@ -300,7 +354,7 @@ extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const
         if (e == cudaSuccess && grad_delta) e = cudaMemsetAsync(grad_delta, 0, sizeof(double), st);
         return cuda_status(e);
     }
-    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, false, true);
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false, true);
     int r = ws_ok(workspace, ws_bytes, L);
     if (r) return r;
     char* ws = static_cast<char*>(workspace);
@@ -308,6 +362,7 @@ extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const
     {
         SweepConsts c = make_consts(*plan);
         for (int k = 0; k < plan->n_e; ++k) sumV += c.v_re[k];
+        sumV *= c.s;  // the derivative channel carries s = 1/sqrt(delta)
     }
     double* D = reinterpret_cast<double*>(ws + L.gD);
     double* A = reinterpret_cast<double*>(ws + L.gA);
@@ -316,15 +371,15 @@ extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const
     const bool need_x = grad_x || grad_delta, need_y = grad_y || grad_delta, need_a = grad_alpha != nullptr;
     if (need_x) {
         // targets x, sources y, strengths alpha: D_i = Re sum V (h+ - h-), A_i coincident sums
-        r = run_pipeline(*plan, x, M, y, alpha, N, nullptr, D, 2, A, ws, L, st);
+        r = run_pipeline(*plan, x, M, y, alpha, N, ItemSource(), nullptr, D, 2, A, ws, L, st);
         if (r) return r;
         if (launch_grad_assemble(grad_u, D, A, sumV, M, gx, st) != cudaSuccess) return FGT1D_ECUDA;
     }
     if (need_a || need_y) {
         // targets y, sources x, strengths grad_u: values -> dL/dalpha, derivative -> dL/dy / alpha
         const int ev = (need_a ? 1 : 0) | (need_y ? 2 : 0);
-        r = run_pipeline(*plan, y, N, x, grad_u, M, grad_alpha, need_y ? D : nullptr, ev, need_y ? A : nullptr, ws, L,
-                         st);
+        r = run_pipeline(*plan, y, N, x, grad_u, M, ItemSource(), grad_alpha, need_y ? D : nullptr, ev,
+                         need_y ? A : nullptr, ws, L, st);
         if (r) return r;
         if (need_y && launch_grad_assemble(alpha, D, A, sumV, N, gy, st) != cudaSuccess) return FGT1D_ECUDA;
     }
@@ -347,7 +402,7 @@ extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t
         std::memset(u_host, 0, sizeof(double) * (size_t)M);
         return FGT1D_OK;
     }
-    Layout L = make_layout(M, N, plan->n_e, plan->flags, true, true);
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, true);
     int r = ws_ok(workspace, ws_bytes, L);
     if (r) return r;
     char* ws = static_cast<char*>(workspace);
@@ -372,15 +427,18 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
     if (!sizes_ok(M, N)) return FGT1D_EINVAL;
     if ((M > 0 && !x) || (N > 0 && !y) || (M + N > 0 && !perm)) return FGT1D_EINVAL;
     if (M + N == 0) return FGT1D_OK;
-    Layout L = make_layout(M, N, 1, FGT1D_FP64, false, false);
+    Layout L = make_layout(M, N, 1, 1, FGT1D_FP64, false, false);
     int r = ws_ok(workspace, ws_bytes, L);
     if (r) return r;
     char* ws = static_cast<char*>(workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws, 0, L.zero_end, st) != cudaSuccess) return FGT1D_ECUDA;
-    SortArgs sa = sort_args(x, M, y, N, ws, L);
+    if (launch_item_single(M, N, 1.0, reinterpret_cast<Item*>(ws + L.items),
+                           reinterpret_cast<int64_t*>(ws + L.header + 80), st) != cudaSuccess)
+        return FGT1D_ECUDA;
+    SortArgs sa = sort_args(x, y, N, ws, L);
     if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
-    return cuda_status(launch_copy_perm(sa, perm, st));
+    return cuda_status(launch_copy_perm(sa, M + N, perm, st));
 }
 
 extern "C" int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream) {
@@ -390,6 +448,7 @@ extern "C" int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream
     uint32_t status = 0;
     if (cudaMemcpy(&status, workspace, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess) return FGT1D_ECUDA;
     if (status && cudaMemset(workspace, 0, sizeof(status)) != cudaSuccess) return FGT1D_ECUDA;
+    if (status & kStatusBadArg) return FGT1D_EINVAL;
     if (status & kStatusNonFinite) return FGT1D_ENONFINITE;
     if (status & kStatusTimeout) return FGT1D_ETIMEOUT;
     return FGT1D_OK;

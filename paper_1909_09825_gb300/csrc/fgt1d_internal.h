@@ -21,6 +21,7 @@ namespace fgt1d {
 enum : uint32_t {
     kStatusNonFinite = 1u,
     kStatusTimeout = 2u,
+    kStatusBadArg = 4u,     // a batch item with a bad delta or negative size
 };
 
 // Degree limit of the per-point Taylor multiplier e^{-tau theta} and the number of

@@ -8,11 +8,56 @@
 
 namespace fgt1d {
 
+// Every kernel works on a batch of independent transforms ("items"; one item for
+// fgt1d_execute).  Item b's merged points [y_b (sources), x_b (targets)] occupy the
+// range [start_b, start_b + nsrc_b + ntgt_b) of the merged arrays, start_b a multiple of
+// kTile; the rest of its padded range [start_b, start_b + ntiles_b * kTile) holds
+// padding that sorts to the end.  A tile therefore never straddles two items and each
+// item's decoupled look-back stays inside its own tiles.
+constexpr int kTile = 4096;
+
+struct Item {
+    int64_t start;    // padded merged offset (multiple of kTile)
+    int64_t nsrc;     // N_b
+    int64_t ntgt;     // M_b
+    int64_t y_off;    // offset of the item's sources in y / alpha
+    int64_t x_off;    // offset of the item's targets in x / u
+    int64_t tile0;    // start / kTile
+    int64_t ntiles;   // padded size / kTile
+    double s;         // 1 / sqrt(delta_b)
+};
+
+// Item b of tile t: the last item whose first tile is <= t (empty items share their
+// successor's first tile and are skipped).
+__device__ __forceinline__ int item_of_tile(const Item* __restrict__ items, int B, int64_t t) {
+    int lo = 0, hi = B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (items[mid].tile0 <= t) lo = mid;
+        else hi = mid;
+    }
+    while (lo + 1 < B && items[lo + 1].tile0 <= t) ++lo;
+    return lo;
+}
+
+// Builds the item table from device offsets x_off/y_off (B+1 entries each) and the
+// per-item bandwidths (device array, or the plan's delta when null).  Writes the total
+// number of tiles to *total_tiles.  An item whose offsets leave [0, M_tot] / [0, N_tot]
+// or decrease, or whose delta is not positive and finite, is left empty and flagged in
+// status; if the items need more than max_tiles tiles (overlapping ranges) none runs.
+cudaError_t launch_items(int B, const int64_t* x_off, const int64_t* y_off, const double* delta, double plan_delta,
+                         Item* items, int64_t* total_tiles, uint32_t* status, int64_t max_tiles, int64_t M_tot,
+                         int64_t N_tot, cudaStream_t st);
+// One item of M targets and N sources with bandwidth delta (fgt1d_execute).
+cudaError_t launch_item_single(int64_t M, int64_t N, double delta, Item* items, int64_t* total_tiles,
+                               cudaStream_t st);
+
 // ---- sort (steps a1-a2) ----
 constexpr int kSortDigits = 8;      // 8-bit digits of a 64-bit key
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 16;
 constexpr int kSortTile = kSortThreads * kSortIPT;
+static_assert(kSortTile == kTile, "sort tiles and item padding share one size");
 // Upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at 2 GHz).
 constexpr long long kSpinLimitCycles = 4000000000LL;
 
@@ -21,26 +66,33 @@ struct SortPlan {
     int32_t src[kSortDigits];   // -1: keys generated from x/y; 0: buffer A; 1: buffer B
     int32_t dst[kSortDigits];
     int32_t final_buf;          // buffer (0 = A, 1 = B) that holds the sorted keys/indices
+    uint32_t active_mask;       // bit d: some item has more than one populated bucket in digit d
 };
 
 struct SortArgs {
     const double* x;
     const double* y;
-    int64_t N, P;
+    int64_t N;            // total number of sources (targets are coded N + i)
+    const Item* items;
+    int B;
+    const int64_t* total_tiles;  // device scalar
+    int64_t max_tiles;    // grid size of the tile kernels (upper bound of *total_tiles)
     uint64_t* keysA;
     uint64_t* keysB;
     uint32_t* valsA;
     uint32_t* valsB;
-    uint32_t* hist;       // [8][256]
-    uint32_t* offs;       // [8][256]
+    uint32_t* hist;       // [B][8][256] per-item digit counts
+    uint32_t* offs;       // [B][8][256] per-item bucket starts (merged positions)
     SortPlan* plan;
     uint64_t* desc;       // [8][desc_stride] look-back words
-    size_t desc_stride;   // tiles * 256
+    size_t desc_stride;   // max_tiles * 256
     uint32_t* tile_ctr;   // [8]
     uint32_t* status;
 };
 
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
+// copies the first P sorted merged codes (item 0) to perm
+cudaError_t launch_copy_perm(const SortArgs& a, int64_t P, uint32_t* perm, cudaStream_t st);
 
 // ---- sweeps (steps a3-a7) ----
 struct TileDesc {           // one (tile, term) entry of the decoupled look-back
@@ -52,38 +104,39 @@ struct TileDesc {           // one (tile, term) entry of the decoupled look-back
 };
 
 struct SweepArgs {
-    int64_t P, N;
+    int64_t N;              // total number of sources
+    const Item* items;
+    int B;
+    const int64_t* total_tiles;
+    int64_t max_tiles;
+    int64_t Ppad;           // padded merged length (multiplier table stride)
     const uint64_t* keysA;
     const uint64_t* keysB;
     const uint32_t* valsA;
     const uint32_t* valsB;
     const SortPlan* plan;
     const double* alpha;
-    double2* mult;          // [n_e][P] multiplier table (FP64 path) or nullptr
-    void* fwd;              // [P] forward partial sums Re sum_k W_k h+_k at targets (double; float on the FP32 path)
-    void* fwd2;             // [P] forward partial sums Re sum_k V_k h+_k (derivative channel)
-    double* u;              // [M] output: Re sum_k W_k (h+ + h-) (value channel)
-    double* out2;           // [M] output: Re sum_k V_k (h+ - h-) (derivative channel)
-    TileDesc* fdesc;        // [tiles][n_e]
-    TileDesc* bdesc;        // [tiles][n_e]
+    double2* mult;          // [n_e][Ppad] multiplier table (FP64 path) or nullptr
+    void* fwd;              // [Ppad] forward partial sums Re sum_k W_k h+_k (double; float on the FP32 path)
+    void* fwd2;             // [Ppad] forward partial sums of the derivative channel
+    double* u;              // output, target order: Re sum_k W_k (h+ + h-) (value channel)
+    double* out2;           // output, target order: s Re sum_k V'_k (h+ - h-) (derivative channel)
+    TileDesc* fdesc;        // [max_tiles][n_e]
+    TileDesc* bdesc;        // [max_tiles][n_e]
     uint32_t* tile_ctr;     // [2]
     uint32_t* status;
-    int64_t tiles;
 };
 
-int sweep_tile_f64();  // points per sweep tile
+int sweep_tile_f64();  // points per sweep tile (== kTile)
 int sweep_tile_f32();
 // Evaluation channels of the sweeps: bit 0 values Re sum W (h+ + h-) into u, bit 1 the
-// derivative Re sum V (h+ - h-) into out2 (V_k = -tau_k s W_k).
+// derivative s Re sum V' (h+ - h-) into out2 (V'_k = -tau_k W_k).
 // `mid` (may be null) is recorded on st between the forward and the backward kernel.
 cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
 cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
 // Coincidence sums: u[i] = sum of alpha over the sources at exactly the coordinate of
 // target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).
 cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
-
-// copies the sorted merged indices (final sort buffer) to perm
-cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st);
 
 // fgt1d_execute on a caller-given workspace (checked against the layout size)
 int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,

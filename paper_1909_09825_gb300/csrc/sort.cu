@@ -35,93 +35,234 @@ __device__ __forceinline__ bool coord_nonfinite(double c) {
     return ((uint64_t)__double_as_longlong(c) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
 }
 
-__device__ __forceinline__ double merged_coord(const double* x, const double* y, int64_t N, int64_t q) {
-    return q < N ? y[q] : x[q - N];
-}
-
-// ---- histogram of all digits --------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sort_hist(const double* __restrict__ x, const double* __restrict__ y,
-                                                   int64_t N, int64_t P, uint32_t* __restrict__ hist,
-                                                   uint32_t* __restrict__ status) {
-    __shared__ uint32_t sh[kSortDigits][256];
-    for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+// ---- item table -----------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_items(int B, const int64_t* __restrict__ x_off,
+                                                const int64_t* __restrict__ y_off, const double* __restrict__ delta,
+                                                double plan_delta, int64_t max_tiles, int64_t M_tot, int64_t N_tot,
+                                                Item* __restrict__ items, int64_t* __restrict__ total_tiles,
+                                                uint32_t* __restrict__ status) {
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    uint32_t last[kSortDigits], run[kSortDigits];
-#pragma unroll
-    for (int d = 0; d < kSortDigits; ++d) { last[d] = 0; run[d] = 0; }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     bool bad = false;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += stride) {
-        double c = merged_coord(x, y, N, q);
-        bad |= coord_nonfinite(c);
-        uint64_t k = coord_key(c);
-#pragma unroll
-        for (int d = 0; d < kSortDigits; ++d) {
-            uint32_t dg = (uint32_t)(k >> (8 * d)) & 255u;
-            if (dg != last[d]) {
-                if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
-                last[d] = dg;
-                run[d] = 0;
+    for (int b0 = 0; b0 < B; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        int64_t nt = 0, nsrc = 0, ntgt = 0, xo = 0, yo = 0;
+        double d = plan_delta;
+        if (b < B) {
+            xo = x_off[b];
+            yo = y_off[b];
+            const int64_t x1 = x_off[b + 1], y1 = y_off[b + 1];
+            if (delta) d = delta[b];
+            if (xo < 0 || x1 < xo || x1 > M_tot || yo < 0 || y1 < yo || y1 > N_tot || !(d > 0.0) || !isfinite(d)) {
+                bad = true;  // the item is left empty
+                xo = yo = 0;
+            } else {
+                nsrc = y1 - yo;
+                ntgt = x1 - xo;
             }
-            ++run[d];
+            nt = (nsrc + ntgt + kTile - 1) / kTile;
         }
-    }
+        // block-wide exclusive scan of nt
+        int64_t inc = nt;
 #pragma unroll
-    for (int d = 0; d < kSortDigits; ++d)
-        if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonFinite);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) {
-        uint32_t v = (&sh[0][0])[i];
-        if (v) atomicAdd(&hist[i], v);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) warp_sum[w] = inc;
+        __syncthreads();
+        int64_t wpre = 0;
+        for (int q = 0; q < w; ++q) wpre += warp_sum[q];
+        const int64_t excl = carry + wpre + inc - nt;
+        if (b < B) {
+            Item it;
+            it.start = excl * kTile;
+            it.nsrc = nsrc;
+            it.ntgt = ntgt;
+            it.y_off = yo;
+            it.x_off = xo;
+            it.tile0 = excl;
+            it.ntiles = nt;
+            it.s = nt ? 1.0 / sqrt(d) : 0.0;
+            items[b] = it;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + nt;
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusBadArg);
+    const int64_t total = carry;
+    if (total > max_tiles) {  // overlapping items: run nothing and report
+        for (int b = threadIdx.x; b < B; b += blockDim.x) items[b].ntiles = 0, items[b].nsrc = 0, items[b].ntgt = 0;
+        if (threadIdx.x == 0) {
+            atomicOr(status, kStatusBadArg);
+            *total_tiles = 0;
+        }
+    } else if (threadIdx.x == 0) {
+        *total_tiles = total;
     }
 }
 
-// ---- bucket offsets and the pass plan (one block of 256 threads) ---------------------------
-__global__ void __launch_bounds__(256) k_sort_plan(const uint32_t* __restrict__ hist, uint32_t* __restrict__ offs,
-                                                   SortPlan* __restrict__ plan, int64_t P) {
+__global__ void k_item_single(int64_t M, int64_t N, double delta, Item* __restrict__ items,
+                              int64_t* __restrict__ total_tiles) {
+    Item it;
+    it.start = 0;
+    it.nsrc = N;
+    it.ntgt = M;
+    it.y_off = 0;
+    it.x_off = 0;
+    it.tile0 = 0;
+    it.ntiles = (M + N + kTile - 1) / kTile;
+    it.s = 1.0 / sqrt(delta);
+    items[0] = it;
+    *total_tiles = it.ntiles;
+}
+
+cudaError_t launch_items(int B, const int64_t* x_off, const int64_t* y_off, const double* delta, double plan_delta,
+                         Item* items, int64_t* total_tiles, uint32_t* status, int64_t max_tiles, int64_t M_tot,
+                         int64_t N_tot, cudaStream_t st) {
+    k_items<<<1, 1024, 0, st>>>(B, x_off, y_off, delta, plan_delta, max_tiles, M_tot, N_tot, items, total_tiles,
+                                status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_item_single(int64_t M, int64_t N, double delta, Item* items, int64_t* total_tiles,
+                               cudaStream_t st) {
+    k_item_single<<<1, 1, 0, st>>>(M, N, delta, items, total_tiles);
+    return cudaGetLastError();
+}
+
+// Key and merged code of padded position g of item `it`: sources first, then targets,
+// then padding (all-ones key, sorted last).
+__device__ __forceinline__ void merged_point(const SortArgs& a, const Item& it, int64_t g, uint64_t& key,
+                                             uint32_t& val, bool& bad) {
+    const int64_t l = g - it.start;
+    if (l < it.nsrc) {
+        const double c = a.y[it.y_off + l];
+        bad |= coord_nonfinite(c);
+        key = coord_key(c);
+        val = (uint32_t)(it.y_off + l);
+    } else if (l < it.nsrc + it.ntgt) {
+        const double c = a.x[it.x_off + (l - it.nsrc)];
+        bad |= coord_nonfinite(c);
+        key = coord_key(c);
+        val = (uint32_t)(a.N + it.x_off + (l - it.nsrc));
+    } else {
+        key = ~0ull;
+        val = 0xFFFFFFFFu;
+    }
+}
+
+// ---- per-item histograms of all digits ----------------------------------------------------
+// Each block walks a contiguous range of tiles, counting in shared memory and flushing
+// the non-zero counts to the current item's histogram when the item changes.
+__global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
+    __shared__ uint32_t sh[kSortDigits][256];
+    __shared__ int s_item;
+    const int64_t T = *a.total_tiles;
+    const int64_t per = (T + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
+    for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+    int cur = -1;
+    bool bad = false;
+    auto flush = [&](int item) {
+        __syncthreads();
+        uint32_t* h = a.hist + (size_t)item * kSortDigits * 256;
+        for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) {
+            const uint32_t v = (&sh[0][0])[i];
+            if (v) {
+                atomicAdd(&h[i], v);
+                (&sh[0][0])[i] = 0;
+            }
+        }
+        __syncthreads();
+    };
+    for (int64_t t = t0; t < t1; ++t) {
+        if (threadIdx.x == 0) s_item = item_of_tile(a.items, a.B, t);
+        __syncthreads();
+        const int item = s_item;
+        if (item != cur) {
+            if (cur >= 0) flush(cur);
+            cur = item;
+        }
+        const Item it = a.items[item];
+        uint32_t last[kSortDigits], run[kSortDigits];
+#pragma unroll
+        for (int d = 0; d < kSortDigits; ++d) { last[d] = 0; run[d] = 0; }
+        for (int e = threadIdx.x; e < kTile; e += blockDim.x) {
+            uint64_t k;
+            uint32_t v;
+            merged_point(a, it, t * kTile + e, k, v, bad);
+#pragma unroll
+            for (int d = 0; d < kSortDigits; ++d) {
+                const uint32_t dg = (uint32_t)(k >> (8 * d)) & 255u;
+                if (dg != last[d]) {
+                    if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
+                    last[d] = dg;
+                    run[d] = 0;
+                }
+                ++run[d];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < kSortDigits; ++d)
+            if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
+        __syncthreads();
+    }
+    if (cur >= 0) flush(cur);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, kStatusNonFinite);
+}
+
+// ---- per-item bucket starts and the digits that need a pass (one block per item) ----------
+__global__ void __launch_bounds__(256) k_sort_plan(SortArgs a) {
     __shared__ uint32_t scan[256];
-    __shared__ int active[kSortDigits];
+    const int b = blockIdx.x;
+    const Item it = a.items[b];
     const int t = threadIdx.x;
+    const int64_t Pb = it.ntiles * kTile;
     for (int d = 0; d < kSortDigits; ++d) {
-        uint32_t v = hist[d * 256 + t];
+        const uint32_t v = a.hist[((size_t)b * kSortDigits + d) * 256 + t];
         scan[t] = v;
         __syncthreads();
         for (int o = 1; o < 256; o <<= 1) {
-            uint32_t add = t >= o ? scan[t - o] : 0;
+            const uint32_t add = t >= o ? scan[t - o] : 0;
             __syncthreads();
             scan[t] += add;
             __syncthreads();
         }
-        offs[d * 256 + t] = scan[t] - v;  // exclusive
-        int full = (P > 0 && (int64_t)v == P);
-        int any_full = __syncthreads_or(full);
-        if (t == 0) active[d] = !any_full;
-        __syncthreads();
+        a.offs[((size_t)b * kSortDigits + d) * 256 + t] = (uint32_t)it.start + scan[t] - v;
+        const int partial = (v != 0 && (int64_t)v != Pb);
+        if (__syncthreads_or(partial) && t == 0) atomicOr(&a.plan->active_mask, 1u << d);
     }
-    if (t == 0) {
-        int cur = -1, n_active = 0;
-        for (int d = 0; d < kSortDigits; ++d) {
-            plan->active[d] = 0;
-            plan->src[d] = 0;
-            plan->dst[d] = 0;
-        }
-        for (int d = 0; d < kSortDigits; ++d) {
-            if (!active[d]) continue;
-            plan->active[d] = 1;
-            plan->src[d] = cur;
-            plan->dst[d] = (cur == 0) ? 1 : 0;
-            cur = plan->dst[d];
-            ++n_active;
-        }
-        if (n_active == 0) {  // every key equal (or P <= 1): one pass materialises keys/indices
-            plan->active[0] = 1;
-            plan->src[0] = -1;
-            plan->dst[0] = 0;
-            cur = 0;
-        }
-        plan->final_buf = cur;
+}
+
+// ---- the pass chain: which buffers each active digit reads and writes -------------------
+__global__ void k_sort_chain(SortPlan* plan) {
+    const uint32_t mask = plan->active_mask;
+    int cur = -1, n_active = 0;
+    for (int d = 0; d < kSortDigits; ++d) {
+        plan->active[d] = 0;
+        plan->src[d] = 0;
+        plan->dst[d] = 0;
     }
+    for (int d = 0; d < kSortDigits; ++d) {
+        if (!((mask >> d) & 1u)) continue;
+        plan->active[d] = 1;
+        plan->src[d] = cur;
+        plan->dst[d] = (cur == 0) ? 1 : 0;
+        cur = plan->dst[d];
+        ++n_active;
+    }
+    if (n_active == 0) {  // every key of every item equal: one pass materialises keys/codes
+        plan->active[0] = 1;
+        plan->src[0] = -1;
+        plan->dst[0] = 0;
+        cur = 0;
+    }
+    plan->final_buf = cur;
 }
 
 // ---- one onesweep digit pass -------------------------------------------------------------
@@ -157,6 +298,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     if (!pl->active[d]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
+    __shared__ int s_item;
     const int src = pl->src[d], dst = pl->dst[d];
     const uint64_t* __restrict__ kin = src == 1 ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vin = src == 1 ? a.valsB : a.valsA;
@@ -165,33 +307,32 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int shift = 8 * d;
 
-    if (tid == 0) sm.tile_id = atomicAdd(&a.tile_ctr[d], 1u);
+    if (tid == 0) {
+        sm.tile_id = atomicAdd(&a.tile_ctr[d], 1u);
+        s_item = (int64_t)sm.tile_id < *a.total_tiles ? item_of_tile(a.items, a.B, sm.tile_id) : -1;
+    }
     for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&sm.wcnt[0][0])[i] = 0;
     __syncthreads();
+    if (s_item < 0) return;
     const uint32_t tile = sm.tile_id;
+    const Item it = a.items[s_item];
     const int64_t base = (int64_t)tile * kSortTile;
-    const int nvalid = (int)min((int64_t)kSortTile, a.P - base);
+    const uint32_t* __restrict__ item_offs = a.offs + ((size_t)s_item * kSortDigits + d) * 256;
 
     // load (warp-striped: warp w owns items [w*32*IPT, (w+1)*32*IPT), slot j covers 32 consecutive items)
     uint64_t key[kSortIPT];
     uint32_t val[kSortIPT];
     uint32_t rank[kSortIPT];
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
         const int li = w * 32 * kSortIPT + j * 32 + lane;
         const int64_t g = base + li;
-        if (li < nvalid) {
-            if (src < 0) {
-                double c = merged_coord(a.x, a.y, a.N, g);
-                key[j] = coord_key(c);
-                val[j] = (uint32_t)g;
-            } else {
-                key[j] = kin[g];
-                val[j] = vin[g];
-            }
+        if (src < 0) {
+            merged_point(a, it, g, key[j], val[j], bad);
         } else {
-            key[j] = 0;
-            val[j] = 0;
+            key[j] = kin[g];
+            val[j] = vin[g];
         }
     }
     // stable warp ranking per slot: the lanes holding the same digit are found with
@@ -201,9 +342,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     unsigned peers[kSortIPT];
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
-        const int li = w * 32 * kSortIPT + j * 32 + lane;
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        unsigned pm = __ballot_sync(0xffffffffu, li < nvalid);
+        unsigned pm = 0xffffffffu;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const unsigned m = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
@@ -214,15 +354,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
-        const int li = w * 32 * kSortIPT + j * 32 + lane;
-        const bool valid = li < nvalid;
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        const uint32_t old = valid ? sm.wcnt[w][dg] : 0u;
+        const uint32_t old = sm.wcnt[w][dg];
         __syncwarp();
-        if (valid) {
-            rank[j] = old + __popc(peers[j] & lt);
-            if ((peers[j] & lt) == 0) sm.wcnt[w][dg] = old + __popc(peers[j]);
-        }
+        rank[j] = old + __popc(peers[j] & lt);
+        if ((peers[j] & lt) == 0) sm.wcnt[w][dg] = old + __popc(peers[j]);
         __syncwarp();
     }
     __syncthreads();
@@ -242,7 +378,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     // exclusive scan of tile counts over digits -> tile_start
     {
         uint32_t v = sm.tile_start[tid];
-        // warp inclusive scan
         uint32_t inc = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -257,15 +392,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
         __syncthreads();
         sm.tile_start[tid] = wpre + inc - v;
     }
-    // decoupled look-back for this digit's global base; each round issues the loads of
-    // kLookAhead predecessors at once so the walk costs one round trip per kLookAhead tiles
+    // decoupled look-back over the item's earlier tiles for this digit's global base;
+    // each round issues the loads of kLookAhead predecessors at once
     {
         constexpr int kLookAhead = 8;
         const int dg = tid;
         uint64_t* desc = a.desc + (size_t)d * a.desc_stride;
         uint32_t excl = 0;
-        if (tile == 0) {
-            st_volatile_u64(&desc[dg], kDescInc | (uint64_t)tot);
+        if ((int64_t)tile == it.tile0) {
+            st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)tot);
         } else {
             st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescAgg | (uint64_t)tot);
             int64_t j = (int64_t)tile - 1;
@@ -274,7 +409,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
                 uint64_t v[kLookAhead];
 #pragma unroll
                 for (int q = 0; q < kLookAhead; ++q)
-                    v[q] = (j - q >= 0) ? ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg]) : kDescInc;
+                    v[q] = (j - q >= it.tile0) ? ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg]) : kDescInc;
 #pragma unroll
                 for (int q = 0; q < kLookAhead; ++q) {
                     if (done) break;
@@ -296,51 +431,46 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
             }
             st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)(excl + tot));
         }
-        sm.gbase[dg] = a.offs[d * 256 + dg] + excl;
+        sm.gbase[dg] = item_offs[dg] + excl;
     }
     __syncthreads();
     // reorder through shared memory
 #pragma unroll
     for (int j = 0; j < kSortIPT; ++j) {
-        const int li = w * 32 * kSortIPT + j * 32 + lane;
-        if (li < nvalid) {
-            const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-            const uint32_t pos = sm.tile_start[dg] + sm.wcnt[w][dg] + rank[j];
-            sm.keys[pos] = key[j];
-            sm.vals[pos] = val[j];
-        }
+        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+        const uint32_t pos = sm.tile_start[dg] + sm.wcnt[w][dg] + rank[j];
+        sm.keys[pos] = key[j];
+        sm.vals[pos] = val[j];
     }
     __syncthreads();
-    for (int i = tid; i < nvalid; i += kSortThreads) {
+    const int64_t item_end = it.start + it.ntiles * kTile;
+    for (int i = tid; i < kSortTile; i += kSortThreads) {
         const uint64_t k = sm.keys[i];
         const uint32_t dg = (uint32_t)(k >> shift) & 255u;
-        const uint32_t o = sm.gbase[dg] + (uint32_t)i - sm.tile_start[dg];
-        if ((int64_t)o < a.P) {  // always true unless a look-back wait timed out
+        const int64_t o = (int64_t)sm.gbase[dg] + i - sm.tile_start[dg];
+        if (o < item_end) {  // always true unless a look-back wait timed out
             kout[o] = k;
             vout[o] = sm.vals[i];
         }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, kStatusNonFinite);
 }
 
 size_t sort_pass_smem() { return sizeof(SortSmem); }
 
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
-    if (a.P <= 0) return cudaSuccess;
+    if (a.max_tiles <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(SortSmem));
     if (e != cudaSuccess) return e;
-    int hist_blocks = (int)std::min<int64_t>((a.P + 255) / 256, 152 * 8);
-    k_sort_hist<<<hist_blocks, 256, 0, st>>>(a.x, a.y, a.N, a.P, a.hist, a.status);
-    k_sort_plan<<<1, 256, 0, st>>>(a.hist, a.offs, a.plan, a.P);
-    const int64_t tiles = (a.P + kSortTile - 1) / kSortTile;
+    const int hist_blocks = (int)std::min<int64_t>(a.max_tiles, 152 * 4);
+    k_sort_hist<<<hist_blocks, 256, 0, st>>>(a);
+    k_sort_plan<<<a.B, 256, 0, st>>>(a);
+    k_sort_chain<<<1, 1, 0, st>>>(a.plan);
     for (int d = 0; d < kSortDigits; ++d)
-        k_sort_pass<<<(unsigned)tiles, kSortThreads, sizeof(SortSmem), st>>>(a, d);
+        k_sort_pass<<<(unsigned)a.max_tiles, kSortThreads, sizeof(SortSmem), st>>>(a, d);
     return cudaGetLastError();
 }
-
-}  // namespace fgt1d
-
-namespace fgt1d {
 
 __global__ void k_copy_perm(const uint32_t* __restrict__ va, const uint32_t* __restrict__ vb, const SortPlan* plan,
                             int64_t P, uint32_t* __restrict__ perm) {
@@ -349,10 +479,10 @@ __global__ void k_copy_perm(const uint32_t* __restrict__ va, const uint32_t* __r
         perm[i] = v[i];
 }
 
-cudaError_t launch_copy_perm(const SortArgs& a, uint32_t* perm, cudaStream_t st) {
-    if (a.P <= 0) return cudaSuccess;
-    int blocks = (int)std::min<int64_t>((a.P + 255) / 256, 152 * 16);
-    k_copy_perm<<<blocks, 256, 0, st>>>(a.valsA, a.valsB, a.plan, a.P, perm);
+cudaError_t launch_copy_perm(const SortArgs& a, int64_t P, uint32_t* perm, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>((P + 255) / 256, 152 * 16);
+    k_copy_perm<<<blocks, 256, 0, st>>>(a.valsA, a.valsB, a.plan, P, perm);
     return cudaGetLastError();
 }
 

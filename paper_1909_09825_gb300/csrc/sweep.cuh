@@ -268,14 +268,15 @@ __device__ __forceinline__ void publish_inc(TileDesc* d, double ir, double ii) {
 }
 
 // Decoupled look-back for term k by one warp over the tiles tile+dir, tile+2 dir, ...
-// (dir = -1 forward, +1 backward), 32 tiles per round trip.  Returns (in every lane)
+// (dir = -1 forward, +1 backward) of the same item ([lo, hi)), 32 tiles per round trip.  Returns (in every lane)
 // the state at the anchor of the adjacent tile:
 //     C = agg_{t1} + M_{t1} (agg_{t2} + M_{t2} (... + M_{tj} inc_{tj}))
 // up to the nearest tile whose inclusive value is published.  Every M is one tile's
 // span multiplier, computed directly from its anchor coordinates when it was published;
 // within a round the products of M are formed by a lane prefix scan.
-static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t tile, int dir, int64_t tiles, int ne,
-                                                   int k, double& Cr, double& Ci, uint32_t* status) {
+static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t tile, int dir, int64_t lo,
+                                                   int64_t hi, int ne, int k, double& Cr, double& Ci,
+                                                   uint32_t* status) {
     const int lane = threadIdx.x & 31;
     double Pr = 1.0, Pi = 0.0;  // product of the span multipliers of the tiles consumed so far
     Cr = 0.0;
@@ -284,7 +285,7 @@ static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t
     bool timed_out = false;
     while (true) {
         const int64_t j = jb + (int64_t)dir * lane;
-        const bool valid = j >= 0 && j < tiles;
+        const bool valid = j >= lo && j < hi;  // the item's own tiles only
         const TileDesc* d = desc + (valid ? j : 0) * ne + k;
         uint32_t f = 2;
         if (valid) {
@@ -400,8 +401,8 @@ __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* _
 // publish aggregate + span multiplier, look back, publish the inclusive value, and
 // leave the state entering each warp in s_win[k][.].
 template <int NE, int NW>
-__device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc, int64_t tile, int dir,
-                                             bool first_in_dir, double Mr, double Mi, double (*s_w)[NW][4],
+__device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc, int64_t tile, int64_t lo, int64_t hi,
+                                             int dir, bool first_in_dir, double Mr, double Mi, double (*s_w)[NW][4],
                                              double (*s_win)[NW][2], int k) {
     const int lane = threadIdx.x & 31;
     double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
@@ -420,7 +421,7 @@ __device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc,
     if (first_in_dir) {
         if (lane == 0) publish_inc(dd, Qr, Qi);
     } else {
-        look_back_warp(desc, tile, dir, a.tiles, NE, k, Cr, Ci, a.status);
+        look_back_warp(desc, tile, dir, lo, hi, NE, k, Cr, Ci, a.status);
         if (lane == 0) {
             double Ir, Ii;
             cfma<double>(Mr, Mi, Cr, Ci, Qr, Qi, Ir, Ii);
@@ -463,17 +464,28 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     __shared__ uint32_t s_tile;
     __shared__ double s_zprev;
 
+    static_assert(TILE == kTile, "a sweep tile is one item tile");
+    __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&a.tile_ctr[0], 1u);
+    if (tid == 0) {
+        s_tile = atomicAdd(&a.tile_ctr[0], 1u);
+        s_item = (int64_t)s_tile < *a.total_tiles ? item_of_tile(a.items, a.B, s_tile) : -1;
+    }
     __syncthreads();
+    if (s_item < 0) return;
+    const Item itm = a.items[s_item];
     const int64_t tile = s_tile;
     const int64_t base = tile * TILE;
-    const int nvalid = (int)min((int64_t)TILE, a.P - base);
+    const int64_t local = base - itm.start;
+    const int nvalid = (int)min((int64_t)TILE, itm.nsrc + itm.ntgt - local);
+    const bool first = local == 0;
+    const double s = itm.s;
+    const float s_f = (float)s;
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
     stage_tile<Real, T, R>(a, keys, vals, base, nvalid, s_z, s_al, s_tgt);
-    if (tid == 0) s_zprev = base > 0 ? key_coord(keys[base - 1]) : 0.0;
+    if (tid == 0) s_zprev = !first ? key_coord(keys[base - 1]) : 0.0;
     __syncthreads();
 
     const int i0 = tid * R;
@@ -485,16 +497,15 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     for (int r = 0; r < R; ++r) {
         const int i = i0 + r;
         Real t = 0;
-        if (i < nvalid && base + i > 0)
-            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], c.s, c.s_f);
+        if (i < nvalid && (i > 0 || !first))
+            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], s, s_f);
         thr[r] = t;
         hw = max(hw, theta_hw<Real>(t));
     }
     hw = __reduce_max_sync(0xffffffffu, hw);
     Real thsp = 0;
-    if (i0 < nvalid && (base > 0 || i0 > 0))
-        thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], c.s,
-                              c.s_f);
+    if (i0 < nvalid && (!first || i0 > 0))
+        thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], s, s_f);
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
 #pragma unroll
@@ -503,14 +514,14 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
     // the tile's span multipliers (lanes of the last warp, one per term)
-    if (tid >= T - NE && tile > 0) {
+    if (tid >= T - NE && !first) {
         const int k = tid - (T - NE);
         double mr, mi;
         if constexpr (CO) {
             mr = zend == zprev ? 1.0 : 0.0;
             mi = 0.0;
         } else {
-            cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (zend - zprev), mr, mi);
+            cexp_neg(c.tau_re[k], c.tau_im[k], s * (zend - zprev), mr, mi);
         }
         s_M[k][0] = mr;
         s_M[k][1] = mi;
@@ -529,7 +540,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
             Mi = 0;
         } else {
             const int deg = taylor_degree<Real>(c, k, hw);
-            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.P + base + i0 : nullptr;
+            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + i0 : nullptr;
             with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll 4
                 for (int r = 0; r < R; ++r) {
@@ -565,8 +576,8 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     __syncthreads();
     // phase B: one lane per term joins the warps and the tiles
     for (int k = w; k < NE; k += NW)
-        tile_combine<NE, NW>(a, a.fdesc, tile, -1, tile == 0, tile > 0 ? s_M[k][0] : 1.0, tile > 0 ? s_M[k][1] : 0.0,
-                             s_w, s_win, k);
+        tile_combine<NE, NW>(a, a.fdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, -1, first, !first ? s_M[k][0] : 1.0,
+                             !first ? s_M[k][1] : 0.0, s_w, s_win, k);
     __syncthreads();
     // phase C: apply the carries, final pass, evaluation at targets.  The value channel
     // accumulates in registers, the derivative channel in shared memory (over the
@@ -606,7 +617,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                 eval(r);
             }
         } else if constexpr (kF64) {
-            const double2* __restrict__ mt = a.mult + (int64_t)k * a.P + base + i0;
+            const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + i0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
@@ -658,13 +669,27 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     __shared__ uint32_t s_tgt[TILE / 32];
     __shared__ uint32_t s_tile;
 
+    static_assert(TILE == kTile, "a sweep tile is one item tile");
+    __shared__ int s_item;
+    __shared__ int64_t s_tilev;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&a.tile_ctr[1], 1u);
+    if (tid == 0) {
+        const int64_t T_tot = *a.total_tiles;
+        const int64_t acq = atomicAdd(&a.tile_ctr[1], 1u);
+        s_tilev = T_tot - 1 - acq;
+        s_item = acq < T_tot ? item_of_tile(a.items, a.B, s_tilev) : -1;
+    }
     __syncthreads();
-    const int64_t tile = a.tiles - 1 - (int64_t)s_tile;
+    if (s_item < 0) return;
+    const Item itm = a.items[s_item];
+    const int64_t tile = s_tilev;
     const int64_t base = tile * TILE;
-    const int nvalid = (int)min((int64_t)TILE, a.P - base);
-    const bool has_next = base + TILE < a.P;
+    const int64_t local = base - itm.start;
+    const int64_t preal = itm.nsrc + itm.ntgt;  // real points of the item
+    const int nvalid = (int)min((int64_t)TILE, preal - local);
+    const bool has_next = local + TILE < preal;
+    const double s = itm.s;
+    const float s_f = (float)s;
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
@@ -682,7 +707,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
             const int i = i0 + r;
             Real t = 0;
             if (i + 1 < nvalid || (i + 1 == TILE && has_next))
-                t = gap_real<Real>(s_z[pad<R>(i)], s_z[pad<R>(i + 1)], c.s, c.s_f);
+                t = gap_real<Real>(s_z[pad<R>(i)], s_z[pad<R>(i + 1)], s, s_f);
             thr[r] = t;
             hw = max(hw, theta_hw<Real>(t));
         }
@@ -692,7 +717,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     {
         const int inext = i0 + R;
         if (i0 < nvalid && (inext < nvalid || (inext == TILE && has_next)))
-            thsp = gap_real<Real>(s_z[pad<R>(i0)], s_z[pad<R>(inext)], c.s, c.s_f);
+            thsp = gap_real<Real>(s_z[pad<R>(i0)], s_z[pad<R>(inext)], s, s_f);
     }
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
@@ -706,7 +731,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     if (tid >= T - NE && has_next) {
         const int k = tid - (T - NE);
         double mr, mi;
-        cexp_neg(c.tau_re[k], c.tau_im[k], c.s * (znext - zfirst), mr, mi);
+        cexp_neg(c.tau_re[k], c.tau_im[k], s * (znext - zfirst), mr, mi);
         s_M[k][0] = mr;
         s_M[k][1] = mi;
     }
@@ -716,7 +741,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     auto mult_at = [&](int k, auto Dc, int r, Real& mr, Real& mi) {
         if constexpr (kF64) {
             const int64_t p = base + i0 + r + 1;
-            const double2 m = p < a.P ? a.mult[(int64_t)k * a.P + p] : make_double2(0.0, 0.0);
+            const double2 m = local + i0 + r + 1 < preal ? a.mult[(int64_t)k * a.Ppad + p] : make_double2(0.0, 0.0);
             mr = m.x;
             mi = m.y;
         } else {
@@ -760,8 +785,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     }
     __syncthreads();
     for (int k = w; k < NE; k += NW)
-        tile_combine<NE, NW>(a, a.bdesc, tile, +1, !has_next, has_next ? s_M[k][0] : 1.0, has_next ? s_M[k][1] : 0.0,
-                             s_w, s_win, k);
+        tile_combine<NE, NW>(a, a.bdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, +1, !has_next,
+                             has_next ? s_M[k][0] : 1.0, has_next ? s_M[k][1] : 0.0, s_w, s_win, k);
     __syncthreads();
     Real acc[R];
 #pragma unroll
@@ -806,8 +831,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                 a.u[t] = kF64 ? (double)(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)])
                               : real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
             if constexpr ((EV & 2) != 0)
-                a.out2[t] = kF64 ? (double)(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)])
-                                 : real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
+                a.out2[t] = s * (kF64 ? (double)(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)])
+                                      : real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]));
         }
     }
 }

@@ -14,9 +14,9 @@ cudaError_t run_sweep_pair(const SweepArgs& a, const SweepConsts& c, cudaStream_
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kf<<<(unsigned)a.tiles, T, smem, st>>>(a, c);
+    kf<<<(unsigned)a.max_tiles, T, smem, st>>>(a, c);
     if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
-    kb<<<(unsigned)a.tiles, T, smem, st>>>(a, c);
+    kb<<<(unsigned)a.max_tiles, T, smem, st>>>(a, c);
     return cudaGetLastError();
 }
 

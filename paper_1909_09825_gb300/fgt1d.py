@@ -229,3 +229,34 @@ def gauss_transform(x, y, alpha, delta, eps=1e-10, precision="fp64"):
         plan = _plans[key] = Plan(d, eps, precision=precision)
     dt = delta if isinstance(delta, torch.Tensor) else torch.tensor(d, dtype=torch.float64)
     return GaussTransform.apply(x, y, alpha, dt, plan)
+
+
+def transform_batched(plan, x_off, y_off, x, y, alpha, delta=None, out=None, workspace=None, stream=None,
+                      sync_check=True):
+    """B independent transforms in one pass (fgt1d_execute_batched).
+
+    x_off, y_off: int64 CUDA tensors of B+1 offsets into x / u and y / alpha;
+    delta: float64 CUDA tensor of B bandwidths, or None for the plan's delta."""
+    for t, n in ((x, "x"), (y, "y"), (alpha, "alpha")):
+        _dev(t, n)
+    if not (x_off.is_cuda and y_off.is_cuda and x_off.dtype == torch.int64 and y_off.dtype == torch.int64):
+        raise TypeError("offsets must be int64 CUDA tensors")
+    B = x_off.numel() - 1
+    if y_off.numel() != B + 1 or B < 1:
+        raise ValueError("x_off and y_off need B + 1 entries")
+    if delta is not None:
+        _dev(delta, "delta")
+    M, N = x.numel(), y.numel()
+    if out is None:
+        out = torch.empty(M, dtype=torch.float64, device=x.device)
+    b = ctypes.c_size_t()
+    check(lib().fgt1d_batched_workspace_size(plan.handle, B, M, N, ctypes.byref(b)), "batched_workspace_size")
+    ws = _workspace(workspace, x.device, b.value)
+    st = _stream_ptr(stream)
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    check(lib().fgt1d_execute_batched(plan.handle, B, p(x_off.contiguous()), p(y_off.contiguous()), p(delta), p(x), M,
+                                      p(y), p(alpha), N, p(out), ctypes.c_void_p(ws.data_ptr()), ws.numel(), st),
+          "execute_batched")
+    if sync_check:
+        check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "execute_batched (device)")
+    return out

@@ -254,6 +254,17 @@ def main():
             also.append({"precision": cfg["precision"], "delta": cfg["delta"], "eps": cfg["eps"], "n_e": p2.n_e,
                          "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2})
 
+    # error of the headline result against the oracle's direct sum at sampled targets
+    head_err = None
+    if rank == 0 and not args.no_cpu:
+        head_err = sampled_error(plan, X, Y, A, x, y, a, HEAD["delta"], dev)
+
+    extra = {}
+    if not args.no_also:
+        extra["precision_split"] = precision_split(args, dev, world, P)
+        extra["differentiation"] = differentiation(dev, world)
+        extra["batched"] = batched(dev, world)
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     hx = torch.from_numpy(x).pin_memory().numpy()
     hy = torch.from_numpy(y).pin_memory().numpy()
@@ -283,13 +294,130 @@ def main():
                            "precision": "fp64", "l2": "inputs (24 B/point, %.1f GB) larger than the 129 MB L2"
                                                        % (24 * P / 2 ** 30 / 1.0),
                            "parallelism": "replicas" if world > 1 else "single"},
-                "stages": stages, "roofline": roofline, "cpu_baseline": cpu,
+                "stages": stages, "error": head_err, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": world * P / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 8 * (M + 2 * N),
                         "d2h_bytes_per_step": 8 * M},
-                "gpu_launches": KERNELS_PER_TRANSFORM * args.steps, "clocks": clocks, "also": also}
+                "gpu_launches": KERNELS_PER_TRANSFORM * args.steps, "clocks": clocks, "also": also, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _event_time(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def sampled_error(plan, X, Y, A, x, y, a, delta, dev, n=8, seed=17):
+    """||u - u_ref||_inf / sum|alpha| over n sampled targets against the oracle's direct sum."""
+    import torch
+    import paper_1909_09825_gb300 as fgt
+    from oracle import oracle
+    u = fgt.transform(plan, X, Y, A)
+    idx = np.random.default_rng(seed).choice(len(x), n, replace=False)
+    ug = u[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    ref = oracle.direct(x[idx], y, a, delta, nthreads=0)
+    return {"max_abs_err_over_sum_abs_alpha": float(np.max(np.abs(ug - ref)) / np.abs(a).sum()),
+            "sampled_targets": n, "reference": "oracle direct FP64 sum over all sources"}
+
+
+def precision_split(args, dev, world, P_unused):
+    """Mixture of 8 Gaussians (sigma 1e-3) + 10% uniform, alpha ~ U(-1,1), delta = 1e-4,
+    M = N = 2^26: FP32 at eps 1e-6 against FP64 at eps 1e-6 and 1e-10, with errors."""
+    import torch
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import inputs
+    M = N = 1 << args.log2
+    x, y, a = inputs.mixture(M, N, seed=0)
+    X, Y, A = (torch.from_numpy(v).to(dev) for v in (x, y, a))
+    out = []
+    U = torch.empty(M, dtype=torch.float64, device=dev)
+    ws = fgt.Workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+    for prec, eps in (("fp32", 1e-6), ("fp64", 1e-6), ("fp64", 1e-10)):
+        plan = fgt.Plan(1e-4, eps, precision=prec)
+        ms = _event_time(lambda: fgt.transform(plan, X, Y, A, out=U, workspace=ws, sync_check=False), 3, 2, stream)
+        err = sampled_error(plan, X, Y, A, x, y, a, 1e-4, dev)
+        out.append({"precision": prec, "eps": eps, "n_e": plan.n_e, "value": world * (M + N) / (ms * 1e-3),
+                    "ms_per_step": ms, "error": err})
+    fp32, fp64 = out[0], out[1]
+    del X, Y, A, U, ws
+    torch.cuda.empty_cache()
+    return {"workload": "mixture of 8 Gaussians (centres U[0,1], sigma 1e-3) + 10%% uniform, M=N=2^%d, "
+                        "alpha ~ U(-1,1), delta=1e-4, seed 0" % args.log2,
+            "runs": out, "fp32_speedup_over_fp64_at_eps_1e-6": fp64["ms_per_step"] / fp32["ms_per_step"]}
+
+
+def differentiation(dev, world, log2=24):
+    """M = N = 2^24, delta = 1e-3, eps = 1e-8, L = sum (u_i - sin(2 pi x_i))^2: forward +
+    backward (dL/dalpha, dL/dx, dL/dy, dL/ddelta) through the adjoint sweeps."""
+    import torch
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import inputs
+    M = N = 1 << log2
+    x, y, a = inputs.uniform(M, N, seed=0)
+    X, Y, A = (torch.from_numpy(v).to(dev) for v in (x, y, a))
+    F = torch.sin(2 * np.pi * X)
+    plan = fgt.Plan(1e-3, 1e-8)
+    ws = fgt.Workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+    U = torch.empty(M, dtype=torch.float64, device=dev)
+
+    def fwd():
+        fgt.transform(plan, X, Y, A, out=U, workspace=ws, sync_check=False)
+
+    def fwd_bwd():
+        fwd()
+        g = 2.0 * (U - F)
+        fgt.backward(plan, X, Y, A, g, workspace=ws, sync_check=False)
+
+    ms_f = _event_time(fwd, 3, 2, stream)
+    ms_fb = _event_time(fwd_bwd, 3, 2, stream)
+    del X, Y, A, F, U, ws
+    torch.cuda.empty_cache()
+    P = M + N
+    return {"workload": "M=N=2^%d uniform, alpha ~ N(0,1), delta=1e-3, eps=1e-8 (n_e=%d), "
+                        "L=sum(u-sin 2 pi x)^2, grads alpha, x, y, delta" % (log2, plan.n_e),
+            "forward_points_per_s": world * P / (ms_f * 1e-3), "forward_ms": ms_f,
+            "forward_backward_points_per_s": world * P / (ms_fb * 1e-3), "forward_backward_ms": ms_fb,
+            "backward_ms": ms_fb - ms_f}
+
+
+def batched(dev, world, B=4096):
+    """B = 4096 transforms, M_b = N_b log-uniform in [1e2, 1e6], delta_b log-uniform in
+    [1e-6, 1e-1], eps = 1e-6 FP64, one pass of the kernels captured in a CUDA graph."""
+    import torch
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import inputs
+    XO, YO, D, X, Y, A, sizes = inputs.batched_device(B, dev, seed=0)
+    P = int(2 * sizes.sum())
+    plan = fgt.Plan(1.0, 1e-6)
+    ws = fgt.Workspace(dev)
+    out = torch.empty_like(X)
+    fgt.transform_batched(plan, XO, YO, X, Y, A, delta=D, out=out, workspace=ws)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fgt.transform_batched(plan, XO, YO, X, Y, A, delta=D, out=out, workspace=ws, stream=s, sync_check=False)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    ms = _event_time(g.replay, 3, 2, torch.cuda.current_stream(dev))
+    del XO, YO, D, X, Y, A, out, ws, g
+    torch.cuda.empty_cache()
+    return {"workload": "B=%d items, M_b=N_b=round(10^U(2,6)), delta_b=10^U(-6,-1), uniform x,y, alpha ~ N(0,1), "
+                        "eps=1e-6 FP64 (n_e=%d), CUDA graph replay" % (B, plan.n_e),
+            "points": P, "value": world * P / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms}
 
 
 def _traffic_record(plan):

@@ -80,3 +80,21 @@ def with_ties(M, N, seed=0, n_distinct=64):
     y = vals[rng.integers(0, n_distinct, N)]
     a = rng.standard_normal(N)
     return x, y, a
+
+
+def batched_device(B, device, seed=0, lo=1e2, hi=1e6, dlo=1e-6, dhi=1e-1):
+    """Batched workload drawn on the device (torch generator) for large B: item sizes
+    M_b = N_b and bandwidths from batched_sizes (numpy, seed), then x, y ~ U[0,1) and
+    alpha ~ N(0,1) from a torch generator seeded with seed + 1.  Returns
+    (x_off, y_off, delta, x, y, alpha) as device tensors and the host sizes."""
+    import torch
+    sizes, deltas = batched_sizes(B, seed, lo, hi, dlo, dhi)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    total = int(off[-1])
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 1)
+    x = torch.rand(total, generator=g, dtype=torch.float64, device=device)
+    y = torch.rand(total, generator=g, dtype=torch.float64, device=device)
+    a = torch.randn(total, generator=g, dtype=torch.float64, device=device)
+    t_off = torch.from_numpy(off).to(device)
+    return t_off, t_off.clone(), torch.from_numpy(deltas).to(device), x, y, a, sizes

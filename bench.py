@@ -45,6 +45,17 @@ WORKLOAD = ("plain FP64 at scale: M=N=2^26, x,y ~ U[0,1), alpha ~ N(0,1), delta=
             "inputs (sort timed), seed 0")
 
 
+def max_over_ranks(value, device=None):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,11 +225,7 @@ def main():
         barrier()
         _lib.check(_lib.lib().fgt1d_check(ctypes.c_void_p(buf.data_ptr()), buf.numel(),
                                           ctypes.c_void_p(stream.cuda_stream)), "bench (device status)")
-        ms = t_start.elapsed_time(t_end) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(t_start.elapsed_time(t_end) / steps, dev)
         stages = None
         if profile:
             st = np.array([[ev[4 * s + i].elapsed_time(ev[4 * s + i + 1]) for i in range(3)] for s in range(steps)])
@@ -424,7 +431,7 @@ def _traffic_record(plan):
     """DRAM bytes per merged point of the forward sweep from the committed ncu summary,
     used only while the kernel source still matches the one that was profiled."""
     import hashlib
-    f = os.path.join(ROOT, "profiles", "sweep_fwd_f64_traffic.json")
+    f = os.path.join(ROOT, "profiles", "sweep_fwd_f64_traffic.txt")
     if not os.path.exists(f):
         return None
     rec = json.load(open(f))

@@ -63,6 +63,8 @@ typedef void* fgt1d_stream;              /* a cudaStream_t */
 #define FGT1D_FP64 0u         /* every step in FP64 */
 #define FGT1D_FP32 1u         /* bulk recurrences in FP32 complex, FP64 coordinate differences
                                  and inter-tile carries; requires eps >= 1e-6 */
+#define FGT1D_EXACT_SELF 2u   /* a source at exactly a target's coordinate contributes
+                                 G(0) = 1 instead of S_n(0) (the paper's codes use S_n(0)) */
 
 #define FGT1D_MAX_TERMS 8     /* largest n_e a plan can hold */
 #define FGT1D_MAX_N 14        /* largest CF order n built in FP64 (Sec. 3.3) */
@@ -80,7 +82,8 @@ int fgt1d_soe_cf(int n, int* n_e, double* tau_re, double* tau_im, double* w_re, 
 
 /* Plan for bandwidth delta and accuracy eps: picks the smallest even n with
  * E_n <= eps (Sec. 3.3), keeps half of the conjugate pairs (Sec. 4) and
- * precomputes the per-term constants.  flags: FGT1D_FP64 or FGT1D_FP32.
+ * precomputes the per-term constants.  flags: FGT1D_FP64 or FGT1D_FP32, optionally
+ * or-ed with FGT1D_EXACT_SELF (fgt1d_execute only).
  * Errors: FGT1D_EINVAL (delta <= 0/non-finite, eps not in (0, 0.5), unknown flags,
  * out == NULL), FGT1D_EUNSUPPORTED (eps < E_n of FGT1D_MAX_N, or FP32 with eps < 1e-6),
  * FGT1D_ENOMEM. */

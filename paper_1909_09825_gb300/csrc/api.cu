@@ -23,7 +23,7 @@ struct Layout {
     size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;
     size_t zero_end = 0;
     size_t items = 0;
-    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0, fwd2 = 0;
+    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0, fwd2 = 0, coinc = 0;
     size_t gD = 0, gA = 0, gx = 0, gy = 0, parts = 0;   // gradients
     size_t hx = 0, hy = 0, ha = 0, hu = 0;              // device copies of host arrays
     size_t total = 0;
@@ -55,6 +55,7 @@ Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sw
     if (sweeps) {
         if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
         L.fwd = off; off += align_up(sizeof(double) * Pp);
+        if (flags & FGT1D_EXACT_SELF) { L.coinc = off; off += align_up(sizeof(double) * (size_t)M); }
     }
     if (grad) {
         const size_t mx = (size_t)std::max(M, N);
@@ -236,7 +237,15 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
                   double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr) {
     if (M == 0) return FGT1D_OK;
     if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
-    return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, evs);
+    if (!(p.flags & FGT1D_EXACT_SELF))
+        return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, evs);
+    // coincident pairs: add (1 - S_n(0)) times the coincident source strengths
+    double* A = reinterpret_cast<double*>(ws + L.coinc);
+    int r = run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, A, ws, L, st, evs);
+    if (r) return r;
+    double s0 = 0.0;
+    for (int k = 0; k < p.n_e; ++k) s0 += p.w_re[k];
+    return cuda_status(launch_axpy(A, 1.0 - s0, M, u, st));
 }
 
 }  // namespace

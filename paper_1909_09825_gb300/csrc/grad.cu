@@ -69,6 +69,18 @@ cudaError_t launch_grad_assemble(const double* w, const double* D, const double*
     return cudaGetLastError();
 }
 
+__global__ void k_axpy(const double* __restrict__ a, double c, int64_t n, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += c * a[i];
+}
+
+cudaError_t launch_axpy(const double* a, double c, int64_t n, double* y, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_axpy<<<blocks, 256, 0, st>>>(a, c, n, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_grad_delta(const double* x, const double* gx, int64_t M, const double* y, const double* gy,
                               int64_t N, double delta, double* partials, int nb, double* out, cudaStream_t st) {
     k_dot_partial<<<nb, 256, 0, st>>>(x, gx, M, y, gy, N, partials);

@@ -146,6 +146,8 @@ size_t transform_workspace_bytes(const fgt1d_plan_s& p, int64_t M, int64_t N);
 // gradient assembly: out[i] = w[i] (D[i] - A[i] sumV)
 cudaError_t launch_grad_assemble(const double* w, const double* D, const double* A, double sumV, int64_t n,
                                  double* out, cudaStream_t st);
+// y[i] += c a[i]
+cudaError_t launch_axpy(const double* a, double c, int64_t n, double* y, cudaStream_t st);
 // *out = -(1/(2 delta)) (sum (x - x[0]) gx + sum (y - x[0]) gy), with nb partial sums
 constexpr int kGradPartials = 608;
 cudaError_t launch_grad_delta(const double* x, const double* gx, int64_t M, const double* y, const double* gy,

@@ -35,12 +35,15 @@ class Plan:
 
     precision: "fp64" (every step in FP64) or "fp32" (FP32-complex recurrences with
     FP64 coordinate differences and inter-tile carries; eps >= 1e-6).
+    exact_self: coincident source/target pairs contribute G(0) = 1 instead of S_n(0).
     """
 
-    def __init__(self, delta, eps=None, precision="fp64", soe=None):
+    def __init__(self, delta, eps=None, precision="fp64", soe=None, exact_self=False):
         if precision not in ("fp64", "fp32"):
             raise ValueError(precision)
         flags = _lib.FGT1D_FP32 if precision == "fp32" else _lib.FGT1D_FP64
+        if exact_self:
+            flags |= _lib.FGT1D_EXACT_SELF
         h = ctypes.c_void_p()
         if soe is None:
             check(lib().fgt1d_plan_create(float(delta), float(eps), flags, ctypes.byref(h)), "plan_create")

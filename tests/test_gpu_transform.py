@@ -179,3 +179,17 @@ def test_repeat_runs_agree(cuda):
     u1 = gpu_transform(plan, x, y, a)
     u2 = gpu_transform(plan, x, y, a)
     assert rel_inf(u1, u2, a) <= TOL_ARITH64
+
+
+def test_exact_self_term(cuda):
+    """FGT1D_EXACT_SELF: coincident pairs get G(0) = 1 (oracle recurrence, exact_self)."""
+    x, y, a = inputs.with_ties(6000, 5000, seed=12, n_distinct=300)
+    delta = 1e-3
+    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    plan = fgt.Plan(delta, soe=(tau, W), exact_self=True)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W, exact_self=True)
+    assert rel_inf(u, ref, a) <= TOL_ARITH64
+    plan2 = fgt.Plan(delta, 1e-8, exact_self=True)
+    u2 = gpu_transform(plan2, x, y, a)
+    assert rel_inf(u2, oracle.direct(x, y, a, delta), a) <= 2e-8 + 1e-13

@@ -31,7 +31,8 @@ LOG2_M = 26
 HEAD = dict(delta=1e-5, eps=1e-6, precision="fp64")
 ALSO = [dict(delta=1e-5, eps=1e-10, precision="fp64"), dict(delta=1e-2, eps=1e-6, precision="fp64"),
         dict(delta=1e-2, eps=1e-10, precision="fp64"), dict(delta=1e-5, eps=1e-3, precision="fp64"),
-        dict(delta=1e-5, eps=1e-6, precision="fp32"), dict(delta=1e-2, eps=1e-6, precision="fp32")]
+        dict(delta=1e-5, eps=1e-6, precision="fp32"), dict(delta=1e-2, eps=1e-6, precision="fp32"),
+        dict(delta=1e-5, eps=1e-6, precision="f32x2"), dict(delta=1e-5, eps=1e-10, precision="f32x2")]
 # FP64 pipe peak: 152 SMs x 2 DFMA/clk/SM (measured by a DFMA throughput probe on this
 # GB300 pool) x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -340,7 +341,8 @@ def sampled_error(plan, X, Y, A, x, y, a, delta, dev, n=8, seed=17):
 
 def precision_split(args, dev, world, P_unused):
     """Mixture of 8 Gaussians (sigma 1e-3) + 10% uniform, alpha ~ U(-1,1), delta = 1e-4,
-    M = N = 2^26: FP32 at eps 1e-6 against FP64 at eps 1e-6 and 1e-10, with errors."""
+    M = N = 2^26: FP32 at eps 1e-6 against FP64 and double-float at eps 1e-6 and 1e-10,
+    with errors."""
     import torch
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import inputs
@@ -351,7 +353,7 @@ def precision_split(args, dev, world, P_unused):
     U = torch.empty(M, dtype=torch.float64, device=dev)
     ws = fgt.Workspace(dev)
     stream = torch.cuda.current_stream(dev)
-    for prec, eps in (("fp32", 1e-6), ("fp64", 1e-6), ("fp64", 1e-10)):
+    for prec, eps in (("fp32", 1e-6), ("fp64", 1e-6), ("fp64", 1e-10), ("f32x2", 1e-6), ("f32x2", 1e-10)):
         plan = fgt.Plan(1e-4, eps, precision=prec)
         ms = _event_time(lambda: fgt.transform(plan, X, Y, A, out=U, workspace=ws, sync_check=False), 3, 2, stream)
         err = sampled_error(plan, X, Y, A, x, y, a, 1e-4, dev)

@@ -65,6 +65,9 @@ typedef void* fgt1d_stream;              /* a cudaStream_t */
                                  and inter-tile carries; requires eps >= 1e-6 */
 #define FGT1D_EXACT_SELF 2u   /* a source at exactly a target's coordinate contributes
                                  G(0) = 1 instead of S_n(0) (the paper's codes use S_n(0)) */
+#define FGT1D_F32X2 4u        /* recurrences in double-float (pairs of FP32, ~48-bit
+                                 significand) with FP64 tile carries: FP64-grade accuracy
+                                 without the FP64 pipe; gradients use the FP64 path */
 
 #define FGT1D_MAX_TERMS 8     /* largest n_e a plan can hold */
 #define FGT1D_MAX_N 14        /* largest CF order n built in FP64 (Sec. 3.3) */
@@ -82,11 +85,11 @@ int fgt1d_soe_cf(int n, int* n_e, double* tau_re, double* tau_im, double* w_re, 
 
 /* Plan for bandwidth delta and accuracy eps: picks the smallest even n with
  * E_n <= eps (Sec. 3.3), keeps half of the conjugate pairs (Sec. 4) and
- * precomputes the per-term constants.  flags: FGT1D_FP64 or FGT1D_FP32, optionally
- * or-ed with FGT1D_EXACT_SELF (fgt1d_execute only).
- * Errors: FGT1D_EINVAL (delta <= 0/non-finite, eps not in (0, 0.5), unknown flags,
- * out == NULL), FGT1D_EUNSUPPORTED (eps < E_n of FGT1D_MAX_N, or FP32 with eps < 1e-6),
- * FGT1D_ENOMEM. */
+ * precomputes the per-term constants.  flags: FGT1D_FP64, FGT1D_FP32 or FGT1D_F32X2,
+ * optionally or-ed with FGT1D_EXACT_SELF (fgt1d_execute only).
+ * Errors: FGT1D_EINVAL (delta <= 0/non-finite, eps not in (0, 0.5), unknown flags or
+ * both FP32 and F32X2, out == NULL), FGT1D_EUNSUPPORTED (eps < E_n of FGT1D_MAX_N, or
+ * FP32 with eps < 1e-6), FGT1D_ENOMEM. */
 int fgt1d_plan_create(double delta, double eps, unsigned flags, fgt1d_plan* out);
 
 /* Plan from a caller-given halved SOE (tau_k, W_k), k < n_e <= FGT1D_MAX_TERMS, with

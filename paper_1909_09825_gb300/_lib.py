@@ -21,6 +21,7 @@ FGT1D_ETOOLARGE = 8
 FGT1D_FP64 = 0
 FGT1D_FP32 = 1
 FGT1D_EXACT_SELF = 2
+FGT1D_F32X2 = 4
 MAX_TERMS = 8
 MAX_N = 14
 

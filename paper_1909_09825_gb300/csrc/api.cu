@@ -53,7 +53,9 @@ Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sw
     L.valsA = off; off += align_up(sizeof(uint32_t) * Pp);
     L.valsB = off; off += align_up(sizeof(uint32_t) * Pp);
     if (sweeps) {
-        if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
+        // the multiplier table serves the FP64 sweeps (transform, and gradients of F32X2 plans)
+        const bool f64_sweeps = !(flags & FGT1D_FP32) && (!(flags & FGT1D_F32X2) || grad);
+        if (f64_sweeps) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
         L.fwd = off; off += align_up(sizeof(double) * Pp);
         if (flags & FGT1D_EXACT_SELF) { L.coinc = off; off += align_up(sizeof(double) * (size_t)M); }
     }
@@ -115,7 +117,11 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
     c.n_e = p.n_e;
     c.s = 1.0 / std::sqrt(p.delta);
     c.s_f = (float)c.s;
-    const double u64 = std::ldexp(1.0, -53), u32 = std::ldexp(1.0, -26);
+    const double u64 = std::ldexp(1.0, -53), u32 = std::ldexp(1.0, -26), u48 = std::ldexp(1.0, -48);
+    auto split = [](double v, float* hl) {
+        hl[0] = (float)v;
+        hl[1] = (float)(v - (double)hl[0]);
+    };
     for (int k = 0; k < p.n_e; ++k) {
         c.tau_re[k] = p.tau_re[k];
         c.tau_im[k] = p.tau_im[k];
@@ -124,6 +130,10 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
         // V'_k = -tau_k W_k (the derivative channel multiplies by s per item)
         c.v_re[k] = -(p.tau_re[k] * p.w_re[k] - p.tau_im[k] * p.w_im[k]);
         c.v_im[k] = -(p.tau_re[k] * p.w_im[k] + p.tau_im[k] * p.w_re[k]);
+        split(c.w_re[k], c.wd_re[k]);
+        split(c.w_im[k], c.wd_im[k]);
+        split(c.v_re[k], c.vd_re[k]);
+        split(c.v_im[k], c.vd_im[k]);
         c.tauf_re[k] = (float)p.tau_re[k];
         c.tauf_im[k] = (float)p.tau_im[k];
         // (-tau)^j / j!
@@ -133,6 +143,10 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
             c.tc_im[k][j] = (double)ai;
             c.tcf_re[k][j] = (float)ar;
             c.tcf_im[k][j] = (float)ai;
+            c.tcd_re_hi[k][j] = (float)(double)ar;
+            c.tcd_re_lo[k][j] = (float)((double)ar - (double)c.tcd_re_hi[k][j]);
+            c.tcd_im_hi[k][j] = (float)(double)ai;
+            c.tcd_im_lo[k][j] = (float)((double)ai - (double)c.tcd_im_hi[k][j]);
             long double nr = (ar * -p.tau_re[k] - ai * -p.tau_im[k]) / (j + 1);
             long double ni = (ar * -p.tau_im[k] + ai * -p.tau_re[k]) / (j + 1);
             ar = nr;
@@ -149,7 +163,14 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
             if (d == 0) {
                 c.theta_hi_lim[k][0] = 0;
                 c.theta_hi_lim_f[k][0] = 0;
+                c.theta_hi_lim_d[k][0] = 0;
                 continue;
+            }
+            {
+                float f48 = (float)(std::pow(fact * u48, 1.0 / d) / at);
+                uint32_t b48;
+                std::memcpy(&b48, &f48, 4);
+                c.theta_hi_lim_d[k][d] = b48 - 1u;
             }
             double th64 = std::pow(fact * u64, 1.0 / d) / at;
             double th32 = std::pow(fact * u32, 1.0 / d) / at;
@@ -219,10 +240,12 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
     w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
     w.status = status;
-    const bool f32 = (p.flags & FGT1D_FP32) != 0;
+    const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
-    e = f32 ? launch_sweeps_f32(w, c, st, mid, ev) : launch_sweeps_f64(w, c, st, mid, ev);
+    if (f32) e = launch_sweeps_f32(w, c, st, mid, ev);
+    else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid);
+    else e = launch_sweeps_f64(w, c, st, mid, ev);
     if (e == cudaSuccess) e = rec(3);
     if (e == cudaSuccess && coinc) {
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);

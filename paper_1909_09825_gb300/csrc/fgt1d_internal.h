@@ -44,6 +44,12 @@ struct SweepConsts {
     // stored as the high 32 bits of the double so that warps compare them as integers.
     uint32_t theta_hi_lim[FGT1D_MAX_TERMS][kTaylorMax + 1];
     uint32_t theta_hi_lim_f[FGT1D_MAX_TERMS][kTaylorMax + 1];   // same for the FP32 path (float bits)
+    // double-float path: coefficients and weights split into hi + lo floats, thresholds
+    // on the bit pattern of the high float
+    float tcd_re_hi[FGT1D_MAX_TERMS][kTaylorMax + 1], tcd_re_lo[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    float tcd_im_hi[FGT1D_MAX_TERMS][kTaylorMax + 1], tcd_im_lo[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    float wd_re[FGT1D_MAX_TERMS][2], wd_im[FGT1D_MAX_TERMS][2], vd_re[FGT1D_MAX_TERMS][2], vd_im[FGT1D_MAX_TERMS][2];
+    uint32_t theta_hi_lim_d[FGT1D_MAX_TERMS][kTaylorMax + 1];
 };
 
 }  // namespace fgt1d

@@ -134,6 +134,8 @@ int sweep_tile_f32();
 // `mid` (may be null) is recorded on st between the forward and the backward kernel.
 cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
 cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
+// Double-float sweeps (value channel only).
+cudaError_t launch_sweeps_df(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
 // Coincidence sums: u[i] = sum of alpha over the sources at exactly the coordinate of
 // target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).
 cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);

@@ -348,7 +348,7 @@ extern "C" int fgt1d_plan_create(double delta, double eps, unsigned flags, fgt1d
     if (!out) return FGT1D_EINVAL;
     *out = nullptr;
     if (!(delta > 0.0) || !std::isfinite(delta) || !(eps > 0.0) || !(eps < 0.5) ||
-        (flags & ~(FGT1D_FP32 | FGT1D_EXACT_SELF)))
+        (flags & ~(FGT1D_FP32 | FGT1D_EXACT_SELF | FGT1D_F32X2)) || ((flags & FGT1D_FP32) && (flags & FGT1D_F32X2)))
         return FGT1D_EINVAL;
     if ((flags & FGT1D_FP32) && eps < 1e-6) return FGT1D_EUNSUPPORTED;
     for (int n = 2; n <= FGT1D_MAX_N; n += 2) {
@@ -380,7 +380,8 @@ extern "C" int fgt1d_plan_create_soe(double delta, int n_e, const double* tau_re
     if (!out) return FGT1D_EINVAL;
     *out = nullptr;
     if (!(delta > 0.0) || !std::isfinite(delta) || n_e < 1 || n_e > FGT1D_MAX_TERMS || !tau_re || !tau_im ||
-        !w_re || !w_im || (flags & ~(FGT1D_FP32 | FGT1D_EXACT_SELF)))
+        !w_re || !w_im || (flags & ~(FGT1D_FP32 | FGT1D_EXACT_SELF | FGT1D_F32X2)) ||
+        ((flags & FGT1D_FP32) && (flags & FGT1D_F32X2)))
         return FGT1D_EINVAL;
     if (!fgt1d::finite_all(tau_re, n_e) || !fgt1d::finite_all(tau_im, n_e) || !fgt1d::finite_all(w_re, n_e) ||
         !fgt1d::finite_all(w_im, n_e))

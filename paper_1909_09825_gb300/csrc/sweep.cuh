@@ -42,6 +42,7 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "fgt1d_internal.h"
 #include "kernels.h"
 
@@ -147,6 +148,7 @@ __device__ __forceinline__ void cexp_neg(float tr, float ti, float th, float& mr
     mi = -mag * sn;
 }
 
+
 template <typename Real>
 struct TermConsts;
 template <>
@@ -156,6 +158,10 @@ struct TermConsts<double> {
     __device__ static __forceinline__ double tau_re(const SweepConsts& c, int k) { return c.tau_re[k]; }
     __device__ static __forceinline__ double tau_im(const SweepConsts& c, int k) { return c.tau_im[k]; }
     __device__ static __forceinline__ uint32_t lim(const SweepConsts& c, int k, int d) { return c.theta_hi_lim[k][d]; }
+    __device__ static __forceinline__ double w_re(const SweepConsts& c, int k) { return c.w_re[k]; }
+    __device__ static __forceinline__ double w_im(const SweepConsts& c, int k) { return c.w_im[k]; }
+    __device__ static __forceinline__ double v_re(const SweepConsts& c, int k) { return c.v_re[k]; }
+    __device__ static __forceinline__ double v_im(const SweepConsts& c, int k) { return c.v_im[k]; }
 };
 template <>
 struct TermConsts<float> {
@@ -164,6 +170,24 @@ struct TermConsts<float> {
     __device__ static __forceinline__ float tau_re(const SweepConsts& c, int k) { return c.tauf_re[k]; }
     __device__ static __forceinline__ float tau_im(const SweepConsts& c, int k) { return c.tauf_im[k]; }
     __device__ static __forceinline__ uint32_t lim(const SweepConsts& c, int k, int d) { return c.theta_hi_lim_f[k][d]; }
+    __device__ static __forceinline__ float w_re(const SweepConsts& c, int k) { return c.wd_re[k][0]; }
+    __device__ static __forceinline__ float w_im(const SweepConsts& c, int k) { return c.wd_im[k][0]; }
+    __device__ static __forceinline__ float v_re(const SweepConsts& c, int k) { return c.vd_re[k][0]; }
+    __device__ static __forceinline__ float v_im(const SweepConsts& c, int k) { return c.vd_im[k][0]; }
+};
+template <>
+struct TermConsts<dfloat> {
+    __device__ static __forceinline__ dfloat tc_re(const SweepConsts& c, int k, int j) {
+        return df_make(c.tcd_re_hi[k][j], c.tcd_re_lo[k][j]);
+    }
+    __device__ static __forceinline__ dfloat tc_im(const SweepConsts& c, int k, int j) {
+        return df_make(c.tcd_im_hi[k][j], c.tcd_im_lo[k][j]);
+    }
+    __device__ static __forceinline__ uint32_t lim(const SweepConsts& c, int k, int d) { return c.theta_hi_lim_d[k][d]; }
+    __device__ static __forceinline__ dfloat w_re(const SweepConsts& c, int k) { return df_make(c.wd_re[k][0], c.wd_re[k][1]); }
+    __device__ static __forceinline__ dfloat w_im(const SweepConsts& c, int k) { return df_make(c.wd_im[k][0], c.wd_im[k][1]); }
+    __device__ static __forceinline__ dfloat v_re(const SweepConsts& c, int k) { return df_make(c.vd_re[k][0], c.vd_re[k][1]); }
+    __device__ static __forceinline__ dfloat v_im(const SweepConsts& c, int k) { return df_make(c.vd_im[k][0], c.vd_im[k][1]); }
 };
 
 template <typename Real>
@@ -174,6 +198,17 @@ __device__ __forceinline__ uint32_t theta_hw<double>(double th) {
 }
 template <>
 __device__ __forceinline__ uint32_t theta_hw<float>(float th) { return __float_as_uint(th); }
+template <>
+__device__ __forceinline__ uint32_t theta_hw<dfloat>(dfloat th) { return __float_as_uint(th.hi); }
+
+// exp(-tau_k theta) beyond the Taylor range of the largest degree (rare)
+template <typename Real>
+__device__ __forceinline__ void cexp_term(const SweepConsts& c, int k, Real th, Real& mr, Real& mi) {
+    cexp_neg(TermConsts<Real>::tau_re(c, k), TermConsts<Real>::tau_im(c, k), th, mr, mi);
+}
+// double-float: in FP64 from the FP64 tau_k (defined below)
+template <>
+__device__ __forceinline__ void cexp_term<dfloat>(const SweepConsts& c, int k, dfloat th, dfloat& mr, dfloat& mi);
 
 template <typename Real>
 struct MaxDegree;
@@ -194,6 +229,8 @@ template <>
 struct MaxDegree<double> { static constexpr int value = kTaylorMax; };
 template <>
 struct MaxDegree<float> { static constexpr int value = 8; };
+template <>
+struct MaxDegree<dfloat> { static constexpr int value = kTaylorMax; };
 
 // exp(-tau_k theta) by a Taylor polynomial of compile-time degree D (Horner, complex
 // coefficients, real theta).  At the largest degree, points beyond its threshold fall
@@ -215,7 +252,7 @@ __device__ __forceinline__ void taylor(const SweepConsts& c, int k, Real th, Rea
     }
     if constexpr (D == MaxDegree<Real>::value) {
         if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D))
-            cexp_neg(TermConsts<Real>::tau_re(c, k), TermConsts<Real>::tau_im(c, k), th, mr, mi);
+            cexp_term<Real>(c, k, th, mr, mi);
     }
 }
 
@@ -364,13 +401,57 @@ template <>
 __device__ __forceinline__ double to_real<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ float to_real<float>(double v) { return f64_to_f32(v); }
+template <>
+__device__ __forceinline__ dfloat to_real<dfloat>(double v) {
+    const float hi = f64_to_f32(v);
+    return df_make(hi, f64_to_f32(v - f32_to_f64(hi)));
+}
+
+// 1/sqrt(delta) in the three precisions (the double-float split costs one DADD)
+struct Scale {
+    double d;
+    float f;
+    dfloat df;
+};
+template <typename Real>
+__device__ __forceinline__ Scale make_scale(double s) {
+    Scale sc;
+    sc.d = s;
+    sc.f = std::is_same<Real, double>::value ? 0.f : f64_to_f32(s);
+    sc.df = std::is_same<Real, dfloat>::value ? to_real<dfloat>(s) : df_make(0.f, 0.f);
+    return sc;
+}
+
+// b - a (b >= a) as a double-float: exact when a and b are normal, of one sign and in
+// one binade (the integer difference of the bit patterns has at most 48 significant
+// bits for neighbours); otherwise through an FP64 subtraction.
+__device__ __forceinline__ dfloat gap_df(double a, double b) {
+    const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+    const uint32_t ea = (uint32_t)(ba >> 52) & 0x7FFu, eb = (uint32_t)(bb >> 52) & 0x7FFu;
+    if (ea == eb && ea != 0 && ea != 0x7FF && ((ba ^ bb) >> 63) == 0) {
+        const uint64_t d = bb >= ba ? bb - ba : ba - bb;
+        const int e2 = (int)ea - 1075;
+        if (d == 0) return df_make(0.f, 0.f);
+        const int msb = 63 - __clzll((long long)d);
+        if (msb <= 23) return df_make(u64_scaled_to_f32(d, e2), 0.f);
+        const int sh = msb - 23;
+        const uint64_t m = (d >> sh) + ((d >> (sh - 1)) & 1ull);
+        const uint64_t dh = m << sh;
+        const float hi = u64_scaled_to_f32(dh, e2);
+        const float lo = d >= dh ? u64_scaled_to_f32(d - dh, e2) : -u64_scaled_to_f32(dh - d, e2);
+        return df_make(hi, lo);
+    }
+    return to_real<dfloat>(b - a);
+}
 
 template <typename Real>
-__device__ __forceinline__ Real gap_real(double a, double b, double s, float s_f);
+__device__ __forceinline__ Real gap_real(double a, double b, const Scale& sc);
 template <>
-__device__ __forceinline__ double gap_real<double>(double a, double b, double s, float) { return s * (b - a); }
+__device__ __forceinline__ double gap_real<double>(double a, double b, const Scale& sc) { return sc.d * (b - a); }
 template <>
-__device__ __forceinline__ float gap_real<float>(double a, double b, double, float s_f) { return s_f * gap_f32(a, b); }
+__device__ __forceinline__ float gap_real<float>(double a, double b, const Scale& sc) { return sc.f * gap_f32(a, b); }
+template <>
+__device__ __forceinline__ dfloat gap_real<dfloat>(double a, double b, const Scale& sc) { return sc.df * gap_df(a, b); }
 
 // Stages the tile: coordinates, strengths (0 at targets) and target bits.  Points past
 // the end get z = 0, alpha = 0 and are not targets.
@@ -442,6 +523,25 @@ template <>
 __device__ __forceinline__ double real_to_f64<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ double real_to_f64<float>(float v) { return f32_to_f64(v); }
+template <>
+__device__ __forceinline__ double real_to_f64<dfloat>(dfloat v) { return f32_to_f64(v.hi) + f32_to_f64(v.lo); }
+
+template <>
+__device__ __forceinline__ void cexp_term<dfloat>(const SweepConsts& c, int k, dfloat th, dfloat& mr, dfloat& mi) {
+    double a, b;
+    cexp_neg(c.tau_re[k], c.tau_im[k], real_to_f64<dfloat>(th), a, b);
+    mr = to_real<dfloat>(a);
+    mi = to_real<dfloat>(b);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real shfl_up(Real v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ dfloat shfl_up<dfloat>(dfloat v, int o) { return df_shfl_up(v, o); }
+template <typename Real>
+__device__ __forceinline__ Real shfl_down(Real v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ dfloat shfl_down<dfloat>(dfloat v, int o) { return df_shfl_down(v, o); }
 
 // EV: evaluation channels (bit 0 values, bit 1 derivative).  CO: coincidence mode
 // (NE = 1, multiplier 1 on zero gaps and 0 otherwise, unit weight; the per-target sums
@@ -451,7 +551,8 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
-    constexpr bool kF64 = sizeof(Real) == 8;
+    constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
     Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gaps, written over s_z
@@ -480,7 +581,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     const int nvalid = (int)min((int64_t)TILE, itm.nsrc + itm.ntgt - local);
     const bool first = local == 0;
     const double s = itm.s;
-    const float s_f = (float)s;
+    const Scale sc = make_scale<Real>(s);
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
@@ -498,14 +599,14 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         const int i = i0 + r;
         Real t = 0;
         if (i < nvalid && (i > 0 || !first))
-            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], s, s_f);
+            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], sc);
         thr[r] = t;
         hw = max(hw, theta_hw<Real>(t));
     }
     hw = __reduce_max_sync(0xffffffffu, hw);
     Real thsp = 0;
     if (i0 < nvalid && (!first || i0 > 0))
-        thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], s, s_f);
+        thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], sc);
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
 #pragma unroll
@@ -556,16 +657,16 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            Real Mor = __shfl_up_sync(0xffffffffu, Mr, o), Moi = __shfl_up_sync(0xffffffffu, Mi, o);
-            Real For = __shfl_up_sync(0xffffffffu, fr, o), Foi = __shfl_up_sync(0xffffffffu, fi, o);
+            Real Mor = shfl_up<Real>(Mr, o), Moi = shfl_up<Real>(Mi, o);
+            Real For = shfl_up<Real>(fr, o), Foi = shfl_up<Real>(fi, o);
             if (lane >= o) {
                 cfma<Real>(Mr, Mi, For, Foi, fr, fi, fr, fi);
                 cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
             }
         }
-        Real Mxr = __shfl_up_sync(0xffffffffu, Mr, 1), Mxi = __shfl_up_sync(0xffffffffu, Mi, 1);
-        Real Fxr = __shfl_up_sync(0xffffffffu, fr, 1), Fxi = __shfl_up_sync(0xffffffffu, fi, 1);
-        if (lane == 0) { Mxr = 1; Mxi = 0; Fxr = 0; Fxi = 0; }
+        Real Mxr = shfl_up<Real>(Mr, 1), Mxi = shfl_up<Real>(Mi, 1);
+        Real Fxr = shfl_up<Real>(fr, 1), Fxi = shfl_up<Real>(fi, 1);
+        if (lane == 0) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
         Real* sc = s_scan + (size_t)k * 4 * T;
         sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 31) {
@@ -586,7 +687,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
-    Real* s_acc2 = kF64 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
     if constexpr ((EV & 2) != 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
@@ -597,8 +698,8 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         Real fr, fi;
         cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
                    sc[2 * T + tid], sc[3 * T + tid], fr, fi);
-        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        const Real Vr = (Real)c.v_re[k], Vi = (Real)c.v_im[k];
+        const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
+        const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
         auto eval = [&](int r) {
             if ((tmask >> r) & 1u) {
                 if constexpr (CO) {
@@ -657,7 +758,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     using SM = SweepSmem<Real, NE, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
-    constexpr bool kF64 = sizeof(Real) == 8;
+    constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
     Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gap between points i and i+1, over s_z
@@ -689,7 +791,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     const int nvalid = (int)min((int64_t)TILE, preal - local);
     const bool has_next = local + TILE < preal;
     const double s = itm.s;
-    const float s_f = (float)s;
+    const Scale sc = make_scale<Real>(s);
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
@@ -707,7 +809,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
             const int i = i0 + r;
             Real t = 0;
             if (i + 1 < nvalid || (i + 1 == TILE && has_next))
-                t = gap_real<Real>(s_z[pad<R>(i)], s_z[pad<R>(i + 1)], s, s_f);
+                t = gap_real<Real>(s_z[pad<R>(i)], s_z[pad<R>(i + 1)], sc);
             thr[r] = t;
             hw = max(hw, theta_hw<Real>(t));
         }
@@ -717,7 +819,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     {
         const int inext = i0 + R;
         if (i0 < nvalid && (inext < nvalid || (inext == TILE && has_next)))
-            thsp = gap_real<Real>(s_z[pad<R>(i0)], s_z[pad<R>(inext)], s, s_f);
+            thsp = gap_real<Real>(s_z[pad<R>(i0)], s_z[pad<R>(inext)], sc);
     }
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
@@ -766,16 +868,16 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            Real Mor = __shfl_down_sync(0xffffffffu, Mr, o), Moi = __shfl_down_sync(0xffffffffu, Mi, o);
-            Real For = __shfl_down_sync(0xffffffffu, br, o), Foi = __shfl_down_sync(0xffffffffu, bi, o);
+            Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);
+            Real For = shfl_down<Real>(br, o), Foi = shfl_down<Real>(bi, o);
             if (lane + o < 32) {
                 cfma<Real>(Mr, Mi, For, Foi, br, bi, br, bi);
                 cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
             }
         }
-        Real Mxr = __shfl_down_sync(0xffffffffu, Mr, 1), Mxi = __shfl_down_sync(0xffffffffu, Mi, 1);
-        Real Fxr = __shfl_down_sync(0xffffffffu, br, 1), Fxi = __shfl_down_sync(0xffffffffu, bi, 1);
-        if (lane == 31) { Mxr = 1; Mxi = 0; Fxr = 0; Fxi = 0; }
+        Real Mxr = shfl_down<Real>(Mr, 1), Mxi = shfl_down<Real>(Mi, 1);
+        Real Fxr = shfl_down<Real>(br, 1), Fxi = shfl_down<Real>(bi, 1);
+        if (lane == 31) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
         Real* sc = s_scan + (size_t)k * 4 * T;
         sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
         if (lane == 0) {
@@ -791,7 +893,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
-    Real* s_acc2 = kF64 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
     if constexpr ((EV & 2) != 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
@@ -802,8 +904,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         Real br, bi;  // state at the first point of the next thread
         cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
                    sc[2 * T + tid], sc[3 * T + tid], br, bi);
-        const Real Wr = (Real)c.w_re[k], Wi = (Real)c.w_im[k];
-        const Real Vr = (Real)c.v_re[k], Vi = (Real)c.v_im[k];
+        const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
+        const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
         const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
         with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll
@@ -828,11 +930,9 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
             const int64_t p = base + i;
             const int64_t t = (int64_t)vals[p] - a.N;
             if constexpr ((EV & 1) != 0)
-                a.u[t] = kF64 ? (double)(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)])
-                              : real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
+                a.u[t] = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
             if constexpr ((EV & 2) != 0)
-                a.out2[t] = s * (kF64 ? (double)(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)])
-                                      : real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]));
+                a.out2[t] = s * real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
         }
     }
 }

@@ -33,15 +33,16 @@ def soe_cf(n):
 class Plan:
     """A transform plan for bandwidth delta and accuracy eps (or a given SOE).
 
-    precision: "fp64" (every step in FP64) or "fp32" (FP32-complex recurrences with
-    FP64 coordinate differences and inter-tile carries; eps >= 1e-6).
+    precision: "fp64" (every step in FP64), "fp32" (FP32-complex recurrences with
+    FP64 coordinate differences and inter-tile carries; eps >= 1e-6) or "f32x2"
+    (double-float recurrences, FP64-grade accuracy; gradients run in FP64).
     exact_self: coincident source/target pairs contribute G(0) = 1 instead of S_n(0).
     """
 
     def __init__(self, delta, eps=None, precision="fp64", soe=None, exact_self=False):
-        if precision not in ("fp64", "fp32"):
+        if precision not in ("fp64", "fp32", "f32x2"):
             raise ValueError(precision)
-        flags = _lib.FGT1D_FP32 if precision == "fp32" else _lib.FGT1D_FP64
+        flags = {"fp64": _lib.FGT1D_FP64, "fp32": _lib.FGT1D_FP32, "f32x2": _lib.FGT1D_F32X2}[precision]
         if exact_self:
             flags |= _lib.FGT1D_EXACT_SELF
         h = ctypes.c_void_p()

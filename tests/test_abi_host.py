@@ -83,6 +83,11 @@ def test_plan_errors(L):
     assert e.value.code == _lib.FGT1D_EINVAL
     assert L.fgt1d_plan_create(ctypes.c_double(1.0), ctypes.c_double(1e-6), 0, None) == _lib.FGT1D_EINVAL
     assert L.fgt1d_plan_create(ctypes.c_double(1.0), ctypes.c_double(1e-6), 8, ctypes.byref(ctypes.c_void_p())) == _lib.FGT1D_EINVAL
+    # FP32 and double-float exclude each other
+    assert L.fgt1d_plan_create(ctypes.c_double(1.0), ctypes.c_double(1e-6), _lib.FGT1D_FP32 | _lib.FGT1D_F32X2,
+                               ctypes.byref(ctypes.c_void_p())) == _lib.FGT1D_EINVAL
+    p = fgt.Plan(1.0, 1e-10, precision="f32x2")
+    assert p.E_n <= 1e-10
     assert L.fgt1d_soe_cf(7, *([None] * 6)) == _lib.FGT1D_EINVAL
 
 

@@ -25,6 +25,9 @@ from gpu_util import gpu_transform, rel_inf
 pytestmark = pytest.mark.gpu
 
 TOL_ARITH64 = 1e-12
+# double-float recurrences: unit roundoff 2^-48 instead of 2^-53, so the FP64 bound
+# above scales by 2^5 = 32
+TOL_ARITH_DF = 32 * TOL_ARITH64
 
 
 def oracle_soe_plan(delta, eps, precision="fp64"):
@@ -133,6 +136,37 @@ def test_fp32_mixture_vs_direct(cuda):
     idx = np.random.default_rng(0).choice(len(x), 300, replace=False)
     ref = oracle.direct(x[idx], y, a, delta)
     assert rel_inf(u[idx], ref, a) <= 2 * eps + 5e-6
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (33, 65), (4097, 3000), (30001, 29999)])
+def test_f32x2_ragged_vs_recurrence(cuda, M, N):
+    """Double-float recurrences against the oracle's FP64 recurrence, same SOE."""
+    x, y, a = inputs.uniform(M, N, seed=M * 5 + N)
+    delta = 1e-3
+    plan, tau, W = oracle_soe_plan(delta, 1e-10, precision="f32x2")
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH_DF
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-10])
+@pytest.mark.parametrize("delta", [1e-5, 1e-1])
+def test_f32x2_vs_direct(cuda, eps, delta):
+    x, y, a = inputs.uniform(20000, 20000, seed=23)
+    plan = fgt.Plan(delta, eps, precision="f32x2")
+    u = gpu_transform(plan, x, y, a)
+    idx = np.random.default_rng(2).choice(len(x), 400, replace=False)
+    ref = oracle.direct(x[idx], y, a, delta)
+    assert rel_inf(u[idx], ref, a) <= 2 * eps + 1e-13
+
+
+def test_f32x2_mixture_and_ties(cuda):
+    """Clustered points (gaps across many binades) and exact ties / signed zeros."""
+    for x, y, a, delta in [(*inputs.mixture(30000, 30000, seed=9), 1e-6), (*inputs.with_ties(5000, 4000, seed=3), 1e-2)]:
+        plan, tau, W = oracle_soe_plan(delta, 1e-10, precision="f32x2")
+        u = gpu_transform(plan, x, y, a)
+        ref = oracle.recurrence(x, y, a, delta, tau, W)
+        assert rel_inf(u, ref, a) <= TOL_ARITH_DF
 
 
 def test_empty_inputs(cuda):

@@ -203,6 +203,7 @@ def main():
     def timed(cfg, steps, warmup, profile=False):
         plan = fgt.Plan(cfg["delta"], cfg["eps"], precision=cfg["precision"])
         buf = ws.get(plan.workspace_size(M, N))
+        tune = plan.autotune(X, Y, A, reps=2, workspace=ws)  # untimed: picks the sweep tile shape
         for _ in range(warmup):
             fgt.transform(plan, X, Y, A, out=U, workspace=ws)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * steps)]
@@ -232,6 +233,9 @@ def main():
             st = np.array([[ev[4 * s + i].elapsed_time(ev[4 * s + i + 1]) for i in range(3)] for s in range(steps)])
             stages = {"sort_ms": float(st[:, 0].mean()), "fwd_sweep_ms": float(st[:, 1].mean()),
                       "bwd_sweep_ms": float(st[:, 2].mean())}
+        if stages is not None:
+            stages["tile_threads"] = plan.tile_threads
+            stages["autotune_ms"] = {str(k): v for k, v in tune.items() if k != "chosen"}
         return plan, ms, stages
 
     gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -413,6 +417,7 @@ def batched(dev, world, B=4096):
     plan = fgt.Plan(1.0, 1e-6)
     ws = fgt.Workspace(dev)
     out = torch.empty_like(X)
+    tune = plan.autotune_batched(XO, YO, X, Y, A, delta=D, reps=2, workspace=ws)
     fgt.transform_batched(plan, XO, YO, X, Y, A, delta=D, out=out, workspace=ws)
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
@@ -426,7 +431,8 @@ def batched(dev, world, B=4096):
     torch.cuda.empty_cache()
     return {"workload": "B=%d items, M_b=N_b=round(10^U(2,6)), delta_b=10^U(-6,-1), uniform x,y, alpha ~ N(0,1), "
                         "eps=1e-6 FP64 (n_e=%d), CUDA graph replay" % (B, plan.n_e),
-            "points": P, "value": world * P / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms}
+            "points": P, "value": world * P / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+            "tile_threads": plan.tile_threads, "autotune_ms": {str(k): v for k, v in tune.items() if k != "chosen"}}
 
 
 def _traffic_record(plan):

@@ -153,6 +153,32 @@ int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const in
                           const double* alpha, int64_t N_total, double* u, void* workspace, size_t ws_bytes,
                           fgt1d_stream stream);
 
+/* Sweep tile shape and its autotuner.  Every sweep tile holds 4096 merged points (the
+ * chunk of the associative scan, Sec. 4 recurrences split per tile); a tile runs as
+ * `threads` threads of 4096 / threads consecutive points each.  threads = 128 (32
+ * points per thread) or 256 (16 points per thread); 0 selects the default of the plan's
+ * precision (FP64: 128, FP32 and F32X2: 256).  Results differ between shapes only by
+ * rounding.  fgt1d_plan_get_tile returns the shape in use (never 0).  Not thread-safe
+ * with a concurrent execute on the same plan.  Errors: FGT1D_EINVAL. */
+int fgt1d_plan_set_tile(fgt1d_plan plan, int threads);
+int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads);
+
+/* Times every tile shape on the caller's own workload and keeps the fastest in the
+ * plan (no counterpart in the paper).  With x_off == NULL the workload is one
+ * transform (fgt1d_execute with M = M_total, N = N_total; B must be 1), otherwise the
+ * batch of fgt1d_execute_batched (same arguments).  Each shape runs once untimed and
+ * then `reps` (>= 1) times, timed with CUDA events on `stream`; u is overwritten and the
+ * call synchronises the stream, so it cannot be captured in a graph (capture the
+ * execute calls after it).  *threads_out (may be NULL) receives the chosen shape and
+ * ms_out (may be NULL, room for 2) the mean milliseconds of shapes 128 and 256.  If
+ * the environment variable FGT1D_TILE_THREADS is 128 or 256 that shape is taken
+ * without timing (ms_out gets -1).  Errors: those of the execute call, or the device
+ * status as fgt1d_check reports it; the plan keeps its previous shape on error. */
+int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off, const double* delta,
+                   const double* x, int64_t M_total, const double* y, const double* alpha, int64_t N_total,
+                   double* u, void* workspace, size_t ws_bytes, int reps, fgt1d_stream stream, int* threads_out,
+                   float* ms_out);
+
 /* The transform of fgt1d_execute for callers that cannot allocate device memory (no
  * counterpart in the paper).  Takes only the inputs and the output: its scratch is a
  * fixed 16 MiB array in the library's device memory, held on every GPU that loads the

@@ -1,7 +1,9 @@
 """In-tree build of libfgt1d.so for sm_103a (nvcc, no cmake).
 
 Each translation unit under csrc/ is compiled in parallel into _build/, then
-linked into paper_1909_09825_gb300/libfgt1d.so.  Rebuilds only what changed.
+linked into paper_1909_09825_gb300/libfgt1d.so.  sweep_inst.cu is compiled once
+per (precision, term count) so that the heavy kernel instantiations spread over
+all cores.  Rebuilds only what changed.
 """
 import os
 import subprocess
@@ -32,8 +34,22 @@ def _headers():
     return max(os.path.getmtime(h) for h in hs)
 
 
+# sweep_inst.cu: precision 0 FP64, 1 FP32, 2 double-float; tile shape 0 (128 x 32),
+# 1 (256 x 16); term counts 1..8
+VARIANTS = {"sweep_inst.cu": [("p%d_s%d_ne%d" % (p, sh, ne),
+                               ["-DFGT_SW_PREC=%d" % p, "-DFGT_SW_SHAPE=%d" % sh, "-DFGT_SW_NE=%d" % ne])
+                              for p in (0, 1, 2) for sh in (0, 1) for ne in range(1, 9)]}
+
+
 def _sources():
-    return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    """(source, object name, extra flags) for every unit to compile."""
+    out = []
+    for f in sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp"))):
+        if f in VARIANTS:
+            out += [(f, "%s.%s.o" % (f, tag), flags) for tag, flags in VARIANTS[f]]
+        else:
+            out.append((f, f + ".o", []))
+    return out
 
 
 def build(verbose=False, extra_flags=()):
@@ -43,14 +59,14 @@ def build(verbose=False, extra_flags=()):
     nvcc = _nvcc()
     jobs = []
     objs = []
-    for src in _sources():
+    for src, oname, vflags in _sources():
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(BUILD, oname)
         objs.append(o)
         if os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), hdr_time) and not extra_flags:
             continue
         if src.endswith(".cu"):
-            cmd = [nvcc, "-c", s, "-o", o] + NVCC_FLAGS + list(extra_flags)
+            cmd = [nvcc, "-c", s, "-o", o] + NVCC_FLAGS + vflags + list(extra_flags)
         else:
             cmd = [nvcc, "-c", s, "-o", o, "-x", "c++", "-Xcompiler", "-fPIC", "-O2", "-std=c++17",
                    "-I", INCLUDE, "-I", CSRC]
@@ -60,6 +76,8 @@ def build(verbose=False, extra_flags=()):
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
+    # the kernel instantiation units (the longest) first
+    jobs.sort(key=lambda cmd: os.path.basename(cmd[2]) not in VARIANTS)
     failed = []
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         for cmd, r in ex.map(run, jobs):

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fgt1d_internal.h"
@@ -188,6 +189,14 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
 
+// Sweep tile shape index (0: 128 threads x 32 points, 1: 256 x 16): the plan's explicit
+// choice, else 256 x 16 for the FP32-pipe kernels and 128 x 32 for the FP64 ones.
+int tile_threads_of(const fgt1d_plan_s& p, bool fp32_pipe) {
+    if (p.tile_threads) return p.tile_threads;
+    return fp32_pipe ? 256 : 128;
+}
+int shape_index(const fgt1d_plan_s& p, bool fp32_pipe) { return tile_threads_of(p, fp32_pipe) == 256 ? 1 : 0; }
+
 // Where the items come from: one item (M targets, N sources, the plan's delta), or B
 // items from device offsets and optional per-item bandwidths.
 struct ItemSource {
@@ -243,9 +252,9 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
-    if (f32) e = launch_sweeps_f32(w, c, st, mid, ev);
-    else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid);
-    else e = launch_sweeps_f64(w, c, st, mid, ev);
+    if (f32) e = launch_sweeps_f32(w, c, st, mid, ev, shape_index(p, true));
+    else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid, shape_index(p, true));
+    else e = launch_sweeps_f64(w, c, st, mid, ev, shape_index(p, false));
     if (e == cudaSuccess) e = rec(3);
     if (e == cudaSuccess && coinc) {
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
@@ -471,6 +480,78 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
     SortArgs sa = sort_args(x, y, N, ws, L);
     if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
     return cuda_status(launch_copy_perm(sa, M + N, perm, st));
+}
+
+extern "C" int fgt1d_plan_set_tile(fgt1d_plan plan, int threads) {
+    if (!plan || (threads != 0 && threads != 128 && threads != 256)) return FGT1D_EINVAL;
+    plan->tile_threads = threads;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads) {
+    if (!plan || !threads) return FGT1D_EINVAL;
+    *threads = tile_threads_of(*plan, (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) != 0);
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off, const double* delta,
+                              const double* x, int64_t M_total, const double* y, const double* alpha, int64_t N_total,
+                              double* u, void* workspace, size_t ws_bytes, int reps, fgt1d_stream stream,
+                              int* threads_out, float* ms_out) {
+    static const int kCandidates[kNumShapes] = {128, 256};
+    if (!plan || reps < 1 || B < 1 || (!x_off && B != 1) || !sizes_ok(M_total, N_total)) return FGT1D_EINVAL;
+    if (ms_out)
+        for (int i = 0; i < kNumShapes; ++i) ms_out[i] = -1.f;
+    const int prev = plan->tile_threads;
+    auto done = [&](int t) {
+        plan->tile_threads = t;
+        if (threads_out) *threads_out = tile_threads_of(*plan, (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) != 0);
+        return FGT1D_OK;
+    };
+    if (const char* env = std::getenv("FGT1D_TILE_THREADS")) {
+        const int t = std::atoi(env);
+        if (t == 128 || t == 256) return done(t);
+    }
+    if (M_total == 0 || N_total == 0) return done(prev);  // nothing runs on the device
+    auto run = [&]() {
+        return x_off ? fgt1d_execute_batched(plan, B, x_off, y_off, delta, x, M_total, y, alpha, N_total, u, workspace,
+                                             ws_bytes, stream)
+                     : fgt1d_execute(plan, x, M_total, y, alpha, N_total, u, workspace, ws_bytes, stream);
+    };
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return FGT1D_ECUDA;
+    }
+    int r = FGT1D_OK, best = 0;
+    float best_ms = 0.f;
+    for (int i = 0; i < kNumShapes && r == FGT1D_OK; ++i) {
+        plan->tile_threads = kCandidates[i];
+        r = run();  // untimed: first-use costs (kernel attributes, caches)
+        if (r == FGT1D_OK) r = fgt1d_check(workspace, ws_bytes, stream);
+        if (r == FGT1D_OK && cudaEventRecord(e0, st) != cudaSuccess) r = FGT1D_ECUDA;
+        for (int k = 0; k < reps && r == FGT1D_OK; ++k) r = run();
+        if (r == FGT1D_OK && cudaEventRecord(e1, st) != cudaSuccess) r = FGT1D_ECUDA;
+        if (r == FGT1D_OK) r = fgt1d_check(workspace, ws_bytes, stream);
+        float ms = 0.f;
+        if (r == FGT1D_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = FGT1D_ECUDA;
+        ms /= (float)reps;
+        if (r == FGT1D_OK) {
+            if (ms_out) ms_out[i] = ms;
+            if (i == 0 || ms < best_ms) {
+                best_ms = ms;
+                best = kCandidates[i];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != FGT1D_OK) {
+        plan->tile_threads = prev;
+        return r;
+    }
+    return done(best);
 }
 
 extern "C" int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream) {

@@ -11,6 +11,7 @@ struct fgt1d_plan_s {
     double delta;
     double E_n;
     unsigned flags;
+    int tile_threads;   // sweep tile shape: 0 (precision default), 128 or 256
     double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
     double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
 };

@@ -127,15 +127,17 @@ struct SweepArgs {
     uint32_t* status;
 };
 
-int sweep_tile_f64();  // points per sweep tile (== kTile)
-int sweep_tile_f32();
 // Evaluation channels of the sweeps: bit 0 values Re sum W (h+ + h-) into u, bit 1 the
 // derivative s Re sum V' (h+ - h-) into out2 (V'_k = -tau_k W_k).
 // `mid` (may be null) is recorded on st between the forward and the backward kernel.
-cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
-cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
+// shape: 0 = 128 threads x 32 points, 1 = 256 threads x 16 points.
+constexpr int kNumShapes = 2;
+cudaError_t launch_sweeps_f64(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev,
+                              int shape);
+cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev,
+                              int shape);
 // Double-float sweeps (value channel only).
-cudaError_t launch_sweeps_df(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid);
+cudaError_t launch_sweeps_df(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int shape);
 // Coincidence sums: u[i] = sum of alpha over the sources at exactly the coordinate of
 // target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).
 cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);

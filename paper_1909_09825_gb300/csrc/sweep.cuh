@@ -232,61 +232,93 @@ struct MaxDegree<float> { static constexpr int value = 8; };
 template <>
 struct MaxDegree<dfloat> { static constexpr int value = kTaylorMax; };
 
-// exp(-tau_k theta) by a Taylor polynomial of compile-time degree D (Horner, complex
-// coefficients, real theta).  At the largest degree, points beyond its threshold fall
-// back to exp/sincos; below it the warp-uniform degree already covers every point.
-template <typename Real, int D>
-__device__ __forceinline__ void taylor(const SweepConsts& c, int k, Real th, Real& mr, Real& mi) {
-    if constexpr (D == 0) {
-        mr = Real(1);
-        mi = Real(0);
-    } else {
-        Real ar = TermConsts<Real>::tc_re(c, k, D), ai = TermConsts<Real>::tc_im(c, k, D);
+// A Taylor degree known only at run time (warp-uniform): the double-float path, whose
+// Horner steps are long enough that a loop costs little and one code path per degree
+// would only grow the kernel.
+struct RtDeg {
+    static constexpr int value = -1;
+    int d;
+};
+
+// exp(-tau_k theta) by a Taylor polynomial of degree Dc (Horner, complex coefficients,
+// real theta).  At the largest degree, points beyond its threshold fall back to
+// exp/sincos; below it the warp-uniform degree already covers every point.
+template <typename Real, typename Dc>
+__device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real th, Real& mr, Real& mi) {
+    if constexpr (Dc::value >= 0) {
+        constexpr int D = Dc::value;
+        if constexpr (D == 0) {
+            mr = Real(1);
+            mi = Real(0);
+        } else {
+            Real ar = TermConsts<Real>::tc_re(c, k, D), ai = TermConsts<Real>::tc_im(c, k, D);
 #pragma unroll
+            for (int j = D - 1; j >= 1; --j) {
+                ar = fma(ar, th, TermConsts<Real>::tc_re(c, k, j));
+                ai = fma(ai, th, TermConsts<Real>::tc_im(c, k, j));
+            }
+            mr = fma(ar, th, Real(1));
+            mi = ai * th;
+        }
+        if constexpr (D == MaxDegree<Real>::value) {
+            if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D)) cexp_term<Real>(c, k, th, mr, mi);
+        }
+    } else {
+        const int D = dc.d;
+        Real ar = TermConsts<Real>::tc_re(c, k, D), ai = TermConsts<Real>::tc_im(c, k, D);
+#pragma unroll 1
         for (int j = D - 1; j >= 1; --j) {
             ar = fma(ar, th, TermConsts<Real>::tc_re(c, k, j));
             ai = fma(ai, th, TermConsts<Real>::tc_im(c, k, j));
         }
-        mr = fma(ar, th, Real(1));
-        mi = ai * th;
-    }
-    if constexpr (D == MaxDegree<Real>::value) {
-        if (theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D))
+        if (D > 0) {
+            mr = fma(ar, th, Real(1));
+            mi = ai * th;
+        } else {
+            mr = Real(1);
+            mi = Real(0);
+        }
+        if (D == MaxDegree<Real>::value && theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D))
             cexp_term<Real>(c, k, th, mr, mi);
     }
 }
 
-// Runs body(integral_constant<int, D>) for the warp-uniform degree deg.
+// Runs body(Dc) for the warp-uniform degree deg: a compile-time degree
+// (integral_constant) on the FP64 / FP32 paths, RtDeg for double-float.
 template <typename Real, typename Body>
 __device__ __forceinline__ void with_degree(int deg, Body&& body) {
-    switch (deg) {
-        case 0: body(std::integral_constant<int, 0>{}); break;
-        case 1: body(std::integral_constant<int, 1>{}); break;
-        case 2: body(std::integral_constant<int, 2>{}); break;
-        case 3: body(std::integral_constant<int, 3>{}); break;
-        case 4: body(std::integral_constant<int, 4>{}); break;
-        case 5: body(std::integral_constant<int, 5>{}); break;
-        case 6: body(std::integral_constant<int, 6>{}); break;
-        case 7: body(std::integral_constant<int, 7>{}); break;
-        default:
-            if constexpr (MaxDegree<Real>::value == 8) {
-                body(std::integral_constant<int, 8>{});
-            } else {
-                switch (deg) {
-                    case 8: body(std::integral_constant<int, 8>{}); break;
-                    case 9: body(std::integral_constant<int, 9>{}); break;
-                    case 10: body(std::integral_constant<int, 10>{}); break;
-                    case 11: body(std::integral_constant<int, 11>{}); break;
-                    default: body(std::integral_constant<int, MaxDegree<Real>::value>{}); break;
+    if constexpr (std::is_same<Real, dfloat>::value) {
+        body(RtDeg{deg});
+    } else {
+        switch (deg) {
+            case 0: body(std::integral_constant<int, 0>{}); break;
+            case 1: body(std::integral_constant<int, 1>{}); break;
+            case 2: body(std::integral_constant<int, 2>{}); break;
+            case 3: body(std::integral_constant<int, 3>{}); break;
+            case 4: body(std::integral_constant<int, 4>{}); break;
+            case 5: body(std::integral_constant<int, 5>{}); break;
+            case 6: body(std::integral_constant<int, 6>{}); break;
+            case 7: body(std::integral_constant<int, 7>{}); break;
+            default:
+                if constexpr (MaxDegree<Real>::value == 8) {
+                    body(std::integral_constant<int, 8>{});
+                } else {
+                    switch (deg) {
+                        case 8: body(std::integral_constant<int, 8>{}); break;
+                        case 9: body(std::integral_constant<int, 9>{}); break;
+                        case 10: body(std::integral_constant<int, 10>{}); break;
+                        case 11: body(std::integral_constant<int, 11>{}); break;
+                        default: body(std::integral_constant<int, MaxDegree<Real>::value>{}); break;
+                    }
                 }
-            }
+        }
     }
 }
 
 // Single multiplier with a runtime degree (thread and tile spans).
 template <typename Real>
 __device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, Real& mr, Real& mi) {
-    with_degree<Real>(deg, [&](auto Dc) { taylor<Real, decltype(Dc)::value>(c, k, th, mr, mi); });
+    with_degree<Real>(deg, [&](auto Dc) { taylor<Real>(c, k, Dc, th, mr, mi); });
 }
 
 __device__ __forceinline__ void publish_agg(TileDesc* d, double ar, double ai, double Mr, double Mi) {
@@ -552,6 +584,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
@@ -646,7 +679,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
 #pragma unroll 4
                 for (int r = 0; r < R; ++r) {
                     Real mr, mi;
-                    taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
+                    taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
                     if constexpr (kF64) {
                         if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
                     }
@@ -681,9 +714,10 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                              !first ? s_M[k][1] : 0.0, s_w, s_win, k);
     __syncthreads();
     // phase C: apply the carries, final pass, evaluation at targets.  The value channel
-    // accumulates in registers, the derivative channel in shared memory (over the
-    // coordinates / gaps, which the FP64 path no longer needs and the FP32 path keeps
-    // in the first half of the region).
+    // accumulates in registers on the table path (FP64) and in the targets' strength
+    // slots otherwise; the derivative channel in shared memory (over the coordinates /
+    // gaps, which the FP64 path no longer needs and the FP32 path keeps in the first
+    // half of the region).
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
@@ -726,22 +760,34 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                 eval(r);
             }
         } else {
+            // recomputed multipliers: the value channel accumulates in the targets' own
+            // (zero) strength slots, so the loop needs no register array and is only
+            // partly unrolled (smaller code per Taylor degree)
             with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
-#pragma unroll
+#pragma unroll kUnrollC
                 for (int r = 0; r < R; ++r) {
                     Real mr, mi;
-                    taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
-                    cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
-                    eval(r);
+                    taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
+                    const bool tg = (tmask >> r) & 1u;
+                    Real* slot = &s_al[pad<R>(i0 + r)];
+                    const Real v = *slot;  // strength at a source, running value at a target
+                    cfma<Real>(mr, mi, fr, fi, tg ? Real(0) : v, Real(0), fr, fi);
+                    if (tg) {
+                        if constexpr ((EV & 1) != 0) *slot = fma(Wr, fr, fma(-Wi, fi, v));
+                        if constexpr ((EV & 2) != 0)
+                            s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+                    }
                 }
             });
         }
     }
     // outputs, written coalesced through shared memory (values staged over s_al)
     __syncthreads();
+    if constexpr (kF64 || CO) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
-    __syncthreads();
+        for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
+        __syncthreads();
+    }
     if constexpr (CO) {
         for (int i = tid; i < nvalid; i += T)
             if ((s_tgt[i >> 5] >> (i & 31)) & 1u) a.u[(int64_t)vals[base + i] - a.N] = real_to_f64<Real>(s_al[pad<R>(i)]);
@@ -759,6 +805,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
@@ -769,7 +816,6 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     __shared__ double s_win[NE][NW][2];
     __shared__ double s_M[NE][2];
     __shared__ uint32_t s_tgt[TILE / 32];
-    __shared__ uint32_t s_tile;
 
     static_assert(TILE == kTile, "a sweep tile is one item tile");
     __shared__ int s_item;
@@ -847,7 +893,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
             mr = m.x;
             mi = m.y;
         } else {
-            taylor<Real, decltype(Dc)::value>(c, k, s_th[pad<R>(i0 + r)], mr, mi);
+            taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
         }
     };
 
@@ -908,23 +954,43 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
         const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
         with_degree<Real>(deg, [&](auto Dc) {
+            if constexpr (kF64) {
 #pragma unroll
-            for (int r = R - 1; r >= 0; --r) {
-                Real mr, mi;
-                mult_at(k, Dc, r, mr, mi);
-                cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
-                if ((tmask >> r) & 1u) {
-                    if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
-                    if constexpr ((EV & 2) != 0)
-                        s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                for (int r = R - 1; r >= 0; --r) {
+                    Real mr, mi;
+                    mult_at(k, Dc, r, mr, mi);
+                    cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+                    if ((tmask >> r) & 1u) {
+                        if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+                        if constexpr ((EV & 2) != 0)
+                            s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                    }
+                }
+            } else {
+                // as in the forward sweep: values accumulate in the targets' strength slots
+#pragma unroll kUnrollC
+                for (int r = R - 1; r >= 0; --r) {
+                    Real mr, mi;
+                    mult_at(k, Dc, r, mr, mi);
+                    const bool tg = (tmask >> r) & 1u;
+                    Real* slot = &s_al[pad<R>(i0 + r)];
+                    const Real v = *slot;
+                    cfma<Real>(mr, mi, br, bi, tg ? Real(0) : v, Real(0), br, bi);
+                    if (tg) {
+                        if constexpr ((EV & 1) != 0) *slot = fma(Wr, br, fma(-Wi, bi, v));
+                        if constexpr ((EV & 2) != 0)
+                            s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                    }
                 }
             }
         });
     }
     __syncthreads();
+    if constexpr (kF64) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
-    __syncthreads();
+        for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
+        __syncthreads();
+    }
     for (int i = tid; i < nvalid; i += T) {
         if ((s_tgt[i >> 5] >> (i & 31)) & 1u) {
             const int64_t p = base + i;

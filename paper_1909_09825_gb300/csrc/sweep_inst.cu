@@ -1,0 +1,61 @@
+// The sweep kernels of one precision, tile shape and term count, compiled once per
+// combination (-DFGT_SW_PREC=0 FP64, 1 FP32, 2 double-float; -DFGT_SW_SHAPE=0 128 x 32,
+// 1 256 x 16; -DFGT_SW_NE=1..8) so that the build runs them in parallel.  Each unit
+// defines sweeps_<prec>_s<shape>_ne<NE>(..., ev), the launcher of the forward +
+// backward pair for evaluation channels ev.
+#include "sweep_launch.cuh"
+
+#if !defined(FGT_SW_PREC) || !defined(FGT_SW_NE) || !defined(FGT_SW_SHAPE)
+#error "sweep_inst.cu is compiled once per precision, tile shape and term count"
+#endif
+
+#define FGT_CAT_(a, b, c, d) a##b##c##d
+#define FGT_CAT(a, b, c, d) FGT_CAT_(a, b, c, d)
+
+namespace fgt1d {
+
+namespace {
+constexpr int kT = Shape<FGT_SW_SHAPE>::T, kR = Shape<FGT_SW_SHAPE>::R;
+}
+
+#if FGT_SW_PREC == 0
+cudaError_t FGT_CAT(sweeps_f64_s, FGT_SW_SHAPE, _ne, FGT_SW_NE)(const SweepArgs& a, const SweepConsts& c,
+                                                                cudaStream_t st, cudaEvent_t mid, int ev) {
+    switch (ev) {
+        case 1: return run_sweep_pair<double, kT, kR, 1, FGT_SW_NE>(a, c, st, mid);
+        case 2: return run_sweep_pair<double, kT, kR, 2, FGT_SW_NE>(a, c, st, mid);
+        case 3: return run_sweep_pair<double, kT, kR, 3, FGT_SW_NE>(a, c, st, mid);
+        default: return cudaErrorInvalidValue;
+    }
+}
+#if FGT_SW_NE == 1 && FGT_SW_SHAPE == 0
+cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st) {
+    const size_t smem = SweepSmem<double, 1, kT64, kR64>::bytes;
+    auto kf = k_sweep_fwd<double, 1, kT64, kR64, 1, true>;
+    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kf<<<(unsigned)a.max_tiles, kT64, smem, st>>>(a, c);
+    return cudaGetLastError();
+}
+#endif
+#elif FGT_SW_PREC == 1
+cudaError_t FGT_CAT(sweeps_f32_s, FGT_SW_SHAPE, _ne, FGT_SW_NE)(const SweepArgs& a, const SweepConsts& c,
+                                                                cudaStream_t st, cudaEvent_t mid, int ev) {
+    switch (ev) {
+        case 1: return run_sweep_pair<float, kT, kR, 1, FGT_SW_NE>(a, c, st, mid);
+        case 2: return run_sweep_pair<float, kT, kR, 2, FGT_SW_NE>(a, c, st, mid);
+        case 3: return run_sweep_pair<float, kT, kR, 3, FGT_SW_NE>(a, c, st, mid);
+        default: return cudaErrorInvalidValue;
+    }
+}
+#elif FGT_SW_PREC == 2
+cudaError_t FGT_CAT(sweeps_df_s, FGT_SW_SHAPE, _ne, FGT_SW_NE)(const SweepArgs& a, const SweepConsts& c,
+                                                               cudaStream_t st, cudaEvent_t mid, int ev) {
+    if (ev != 1) return cudaErrorInvalidValue;
+    return run_sweep_pair<dfloat, kT, kR, 1, FGT_SW_NE>(a, c, st, mid);
+}
+#else
+#error "FGT_SW_PREC must be 0, 1 or 2"
+#endif
+
+}  // namespace fgt1d

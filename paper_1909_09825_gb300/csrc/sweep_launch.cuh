@@ -20,25 +20,14 @@ cudaError_t run_sweep_pair(const SweepArgs& a, const SweepConsts& c, cudaStream_
     return cudaGetLastError();
 }
 
-template <typename Real, int T, int R, int EV>
-cudaError_t run_sweeps_ne(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {
-    switch (c.n_e) {
-        case 1: return run_sweep_pair<Real, T, R, EV, 1>(a, c, st, mid);
-        case 2: return run_sweep_pair<Real, T, R, EV, 2>(a, c, st, mid);
-        case 3: return run_sweep_pair<Real, T, R, EV, 3>(a, c, st, mid);
-        case 4: return run_sweep_pair<Real, T, R, EV, 4>(a, c, st, mid);
-        case 5: return run_sweep_pair<Real, T, R, EV, 5>(a, c, st, mid);
-        case 6: return run_sweep_pair<Real, T, R, EV, 6>(a, c, st, mid);
-        case 7: return run_sweep_pair<Real, T, R, EV, 7>(a, c, st, mid);
-        case 8: return run_sweep_pair<Real, T, R, EV, 8>(a, c, st, mid);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-// Tile shapes: FP64 128 threads x 32 points, FP32 256 threads x 16 points.
-constexpr int kT64 = 128, kR64 = 32, kT32 = 256, kR32 = 16;
-
-cudaError_t launch_sweeps_f64_ev(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
-cudaError_t launch_sweeps_f32_ev(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int ev);
+// Tile shapes (threads x points per thread, 4096 points): shape 0 = 128 x 32,
+// shape 1 = 256 x 16.  The coincidence scan runs as 128 x 32.
+constexpr int kT64 = 128, kR64 = 32;
+template <int S>
+struct Shape;
+template <>
+struct Shape<0> { static constexpr int T = 128, R = 32; };
+template <>
+struct Shape<1> { static constexpr int T = 256, R = 16; };
 
 }  // namespace fgt1d

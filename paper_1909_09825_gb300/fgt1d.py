@@ -69,6 +69,47 @@ class Plan:
     def handle(self):
         return self._h
 
+    @property
+    def tile_threads(self):
+        """Threads per 4096-point sweep tile in use (128: 32 points each, 256: 16)."""
+        t = ctypes.c_int()
+        check(lib().fgt1d_plan_get_tile(self._h, ctypes.byref(t)), "plan_get_tile")
+        return t.value
+
+    @tile_threads.setter
+    def tile_threads(self, threads):
+        check(lib().fgt1d_plan_set_tile(self._h, int(threads or 0)), "plan_set_tile")
+
+    def autotune(self, x, y, alpha, reps=3, workspace=None, stream=None):
+        """Times each sweep tile shape on this workload (fgt1d_autotune) and keeps the
+        fastest; returns {threads: mean ms}.  Overwrites nothing of the caller's."""
+        for t, n in ((x, "x"), (y, "y"), (alpha, "alpha")):
+            _dev(t, n)
+        M, N = x.numel(), y.numel()
+        out = torch.empty(M, dtype=torch.float64, device=x.device)
+        ws = _workspace(workspace, x.device, self.workspace_size(M, N))
+        return self._autotune(1, None, None, None, x, M, y, alpha, N, out, ws, reps, stream)
+
+    def autotune_batched(self, x_off, y_off, x, y, alpha, delta=None, reps=3, workspace=None, stream=None):
+        """fgt1d_autotune on a batch (arguments as transform_batched)."""
+        B = x_off.numel() - 1
+        M, N = x.numel(), y.numel()
+        b = ctypes.c_size_t()
+        check(lib().fgt1d_batched_workspace_size(self._h, B, M, N, ctypes.byref(b)), "batched_workspace_size")
+        ws = _workspace(workspace, x.device, b.value)
+        out = torch.empty(M, dtype=torch.float64, device=x.device)
+        return self._autotune(B, x_off.contiguous(), y_off.contiguous(), delta, x, M, y, alpha, N, out, ws, reps,
+                              stream)
+
+    def _autotune(self, B, x_off, y_off, delta, x, M, y, alpha, N, out, ws, reps, stream):
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        chosen = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        check(lib().fgt1d_autotune(self._h, B, p(x_off), p(y_off), p(delta), p(x), M, p(y), p(alpha), N, p(out),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), int(reps), _stream_ptr(stream),
+                                   ctypes.byref(chosen), ms), "autotune")
+        return {128: ms[0], 256: ms[1], "chosen": chosen.value}
+
     def workspace_size(self, M, N, host=False):
         b = ctypes.c_size_t()
         f = lib().fgt1d_workspace_size_host if host else lib().fgt1d_workspace_size

@@ -91,6 +91,26 @@ def test_plan_errors(L):
     assert L.fgt1d_soe_cf(7, *([None] * 6)) == _lib.FGT1D_EINVAL
 
 
+def test_tile_shape_setting(L):
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    assert fgt.Plan(1.0, 1e-6).tile_threads == 128
+    assert fgt.Plan(1.0, 1e-6, precision="fp32").tile_threads == 256
+    p = fgt.Plan(1.0, 1e-10, precision="f32x2")
+    assert p.tile_threads == 256
+    p.tile_threads = 128
+    assert p.tile_threads == 128
+    p.tile_threads = 0
+    assert p.tile_threads == 256
+    for bad in (64, 512, -1):
+        with pytest.raises(_lib.FGTError) as e:
+            p.tile_threads = bad
+        assert e.value.code == _lib.FGT1D_EINVAL
+    assert L.fgt1d_plan_set_tile(None, 128) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_autotune(p.handle, 1, None, None, None, None, 0, None, None, 0, None, None, 0, 0, None, None,
+                            None) == _lib.FGT1D_EINVAL  # reps < 1
+
+
 def test_workspace_size_and_bounds(L):
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import _lib

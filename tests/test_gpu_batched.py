@@ -135,6 +135,22 @@ def test_batched_cuda_graph_replay(cuda):
         assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.abs(a).sum()
 
 
+def test_batched_autotune(cuda):
+    rng = np.random.default_rng(12)
+    B = 64
+    sx = rng.integers(100, 20000, B)
+    b = _batch(sx, sx, 10.0 ** rng.uniform(-5, -2, B), 13)
+    x_off, y_off, d, x, y, a = b
+    T = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(cuda)
+    plan = fgt.Plan(1.0, 1e-8)
+    res = plan.autotune_batched(T(x_off), T(y_off), T(x), T(y), T(a), delta=T(d), reps=2)
+    assert res["chosen"] in (128, 256) and plan.tile_threads == res["chosen"]
+    u = _run(plan, b, cuda)
+    plan.tile_threads = 384 - res["chosen"]  # the other shape
+    u2 = _run(plan, b, cuda)
+    assert np.max(np.abs(u - u2)) <= TOL_ARITH64 * np.abs(a).sum()
+
+
 def test_batched_bad_items(cuda):
     plan = fgt.Plan(1e-3, 1e-6)
     b = _batch([100, 200], [150, 50], [1e-3, -1.0], 10)  # second item: negative delta

@@ -41,6 +41,19 @@ def test_backward_vs_oracle_soe_gradients(cuda, M, N, delta, prec):
     assert abs(gd[0] - rd) <= tol * (1 + kappa) * mag
 
 
+def test_backward_tile_shapes_agree(cuda):
+    x, y, a = inputs.uniform(3000, 2500, seed=5)
+    g = np.random.default_rng(2).standard_normal(3000)
+    out = []
+    for tile in (128, 256):
+        plan = fgt.Plan(1e-3, 1e-8)
+        plan.tile_threads = tile
+        out.append([t.cpu().numpy() for t in fgt.backward(plan, _dev(x, cuda), _dev(y, cuda), _dev(a, cuda),
+                                                          _dev(g, cuda))])
+    for r0, r1 in zip(*out):
+        assert np.max(np.abs(r0 - r1)) <= 1e-11 * max(1.0, np.max(np.abs(r0)))
+
+
 def test_backward_vs_gaussian_direct(cuda):
     """M = N = 2000, delta = 1e-3, eps = 1e-8: dL/dalpha within eps sum|g| of the
     Gaussian's; dL/dx, dL/dy, dL/ddelta within the derivative error of the SOE

@@ -169,6 +169,33 @@ def test_f32x2_mixture_and_ties(cuda):
         assert rel_inf(u, ref, a) <= TOL_ARITH_DF
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f32x2"])
+@pytest.mark.parametrize("tile", [128, 256])
+def test_tile_shapes_vs_recurrence(cuda, prec, tile):
+    """Both sweep tile shapes (128 x 32 and 256 x 16 points) in every precision."""
+    x, y, a = inputs.uniform(12345, 6789, seed=31)
+    delta = 1e-3
+    plan, tau, W = oracle_soe_plan(delta, 1e-6 if prec == "fp32" else 1e-10, precision=prec)
+    plan.tile_threads = tile
+    assert plan.tile_threads == tile
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= {"fp64": TOL_ARITH64, "f32x2": TOL_ARITH_DF, "fp32": 5e-6}[prec]
+
+
+def test_autotune_picks_the_faster_shape(cuda):
+    x, y, a = inputs.uniform(300000, 300000, seed=3)
+    X, Y, A = (torch.from_numpy(v).to(cuda) for v in (x, y, a))
+    delta = 1e-4
+    plan = fgt.Plan(delta, 1e-6)
+    res = plan.autotune(X, Y, A, reps=2)
+    assert res[128] > 0 and res[256] > 0
+    assert res["chosen"] == (128 if res[128] <= res[256] else 256) == plan.tile_threads
+    u = fgt.transform(plan, X, Y, A).cpu().numpy()
+    idx = np.random.default_rng(1).choice(len(x), 64, replace=False)
+    assert rel_inf(u[idx], oracle.direct(x[idx], y, a, delta), a) <= 2e-6 + 1e-13
+
+
 def test_empty_inputs(cuda):
     plan = fgt.Plan(1e-3, 1e-6)
     d = cuda

@@ -158,6 +158,15 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
         // |tau theta|, so along a sweep it cannot accumulate past u sum |tau theta|, i.e.
         // u (|tau| / Re tau) times the decay length, a few tens of ulps.
         const double at = std::hypot(p.tau_re[k], p.tau_im[k]);
+        {
+            double f = 1.0;
+            c.theta_split_d[k][0] = 0;
+            for (int J = 1; J <= kTaylorMax; ++J) {
+                f *= (J + 1);
+                const float fs = (float)(std::pow(std::ldexp(f, -28), 1.0 / (J + 1)) / at);
+                std::memcpy(&c.theta_split_d[k][J], &fs, 4);
+            }
+        }
         double fact = 1.0;
         for (int d = 0; d <= kTaylorMax; ++d) {
             fact *= (d + 1);

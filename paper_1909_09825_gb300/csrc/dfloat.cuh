@@ -69,6 +69,26 @@ __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
     return fast_two_sum(s, e);
 }
 
+// a * b + c left unnormalised (hi + lo with |lo| up to a few ulp(hi)): an operand for
+// the next fma or +, which renormalise
+__device__ __forceinline__ dfloat fma_nr(dfloat a, dfloat b, dfloat c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(p, c.hi, s, e);
+    return df_make(s, __fadd_rn(e, __fadd_rn(pe, c.lo)));
+}
+// a * b left unnormalised
+__device__ __forceinline__ dfloat mul_nr(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    return df_make(p, pe);
+}
+
 __device__ __forceinline__ bool operator==(dfloat a, dfloat b) { return a.hi == b.hi && a.lo == b.lo; }
 
 __device__ __forceinline__ dfloat df_shfl_up(dfloat v, int o) {

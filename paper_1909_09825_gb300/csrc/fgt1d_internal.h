@@ -51,6 +51,9 @@ struct SweepConsts {
     float tcd_im_hi[FGT1D_MAX_TERMS][kTaylorMax + 1], tcd_im_lo[FGT1D_MAX_TERMS][kTaylorMax + 1];
     float wd_re[FGT1D_MAX_TERMS][2], wd_im[FGT1D_MAX_TERMS][2], vd_re[FGT1D_MAX_TERMS][2], vd_im[FGT1D_MAX_TERMS][2];
     uint32_t theta_hi_lim_d[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    // double-float: largest theta (float bits) for which the Taylor terms beyond degree J
+    // can be summed in FP32, |tau_k theta|^(J+1) / (J+1)! <= 2^-28 (index J = 1..kTaylorMax)
+    uint32_t theta_split_d[FGT1D_MAX_TERMS][kTaylorMax + 1];
 };
 
 }  // namespace fgt1d

@@ -131,6 +131,38 @@ __device__ __forceinline__ void cmul(Real ar, Real ai, Real br, Real bi, Real& o
     outr = r;
     outi = i;
 }
+// double-float: inner products left unnormalised, the outer fma renormalises
+template <>
+__device__ __forceinline__ void cfma<dfloat>(dfloat ar, dfloat ai, dfloat br, dfloat bi, dfloat cr, dfloat ci,
+                                             dfloat& outr, dfloat& outi) {
+    const dfloat r = fma(ar, br, fma_nr(-ai, bi, cr));
+    const dfloat i = fma(ar, bi, fma_nr(ai, br, ci));
+    outr = r;
+    outi = i;
+}
+template <>
+__device__ __forceinline__ void cmul<dfloat>(dfloat ar, dfloat ai, dfloat br, dfloat bi, dfloat& outr, dfloat& outi) {
+    const dfloat r = fma(ar, br, -mul_nr(ai, bi));
+    const dfloat i = fma(ar, bi, mul_nr(ai, br));
+    outr = r;
+    outi = i;
+}
+
+// out = a * b + c for a real addend c (the recurrence step m F + alpha)
+template <typename Real>
+__device__ __forceinline__ void cfma_ra(Real ar, Real ai, Real br, Real bi, Real cr, Real& outr, Real& outi) {
+    cfma<Real>(ar, ai, br, bi, cr, Real(0), outr, outi);
+}
+// double-float: the inner products stay unnormalised (fma_nr) and the imaginary part
+// has no addend
+template <>
+__device__ __forceinline__ void cfma_ra<dfloat>(dfloat ar, dfloat ai, dfloat br, dfloat bi, dfloat cr, dfloat& outr,
+                                                dfloat& outi) {
+    const dfloat r = fma(ar, br, fma_nr(-ai, bi, cr));
+    const dfloat i = fma(ar, bi, mul_nr(ai, br));
+    outr = r;
+    outi = i;
+}
 
 // exp(-tau theta) for any theta >= 0, the anchor / span multiplier.
 __device__ __forceinline__ void cexp_neg(double tr, double ti, double th, double& mr, double& mi) {
@@ -213,6 +245,9 @@ __device__ __forceinline__ void cexp_term<dfloat>(const SweepConsts& c, int k, d
 template <typename Real>
 struct MaxDegree;
 
+// The double-float degree carries the split J (see taylor_split) in its bits 8 and up.
+constexpr int kSplitShift = 8;
+
 // Taylor degree for term k that covers every theta whose bit pattern is <= hw.
 template <typename Real>
 __device__ __forceinline__ int taylor_degree(const SweepConsts& c, int k, uint32_t hw) {
@@ -220,6 +255,13 @@ __device__ __forceinline__ int taylor_degree(const SweepConsts& c, int k, uint32
 #pragma unroll
     for (int d = MaxDegree<Real>::value - 1; d >= 0; --d)
         if (hw <= TermConsts<Real>::lim(c, k, d)) deg = d;
+    if constexpr (std::is_same<Real, dfloat>::value) {
+        int J = kTaylorMax;
+#pragma unroll
+        for (int j = kTaylorMax - 1; j >= 1; --j)
+            if (hw <= c.theta_split_d[k][j]) J = j;
+        deg |= J << kSplitShift;
+    }
     return deg;
 }
 
@@ -232,12 +274,70 @@ struct MaxDegree<float> { static constexpr int value = 8; };
 template <>
 struct MaxDegree<dfloat> { static constexpr int value = kTaylorMax; };
 
+// Double-float exp(-tau_k theta) of degree D split at J (1 <= J): the head
+// 1 + sum_{j<=J} c_j theta^j in double-float, the tail theta^(J+1) sum_{j>J} c_j theta^(j-J-1)
+// in FP32 Horner.  J is chosen so that |tau_k theta|^(J+1) / (J+1)! <= 2^-28, which keeps
+// the tail's rounding (at most (D + 1) 2^-24 relative) below 2^-48; c_j = (-tau_k)^j / j!.
+template <typename Real>
+__device__ __forceinline__ void taylor_split(const SweepConsts&, int, int, int, Real, Real&, Real&) {}
+template <>
+__device__ __forceinline__ void taylor_split<dfloat>(const SweepConsts& c, int k, int D, int J, dfloat th, dfloat& mr,
+                                                     dfloat& mi) {
+    const float t = th.hi;
+    float tr = 0.f, ti = 0.f;  // the tail
+    if (D > J) {
+        float ar = c.tcf_re[k][D], ai = c.tcf_im[k][D], tp = t;
+#pragma unroll 1
+        for (int j = D - 1; j > J; --j) {
+            ar = __fmaf_rn(ar, t, c.tcf_re[k][j]);
+            ai = __fmaf_rn(ai, t, c.tcf_im[k][j]);
+        }
+#pragma unroll 1
+        for (int j = 0; j < J; ++j) tp = __fmul_rn(tp, t);
+        tr = __fmul_rn(ar, tp);
+        ti = __fmul_rn(ai, tp);
+    } else {
+        J = D;
+    }
+    if (J == 0) {
+        mr = dfloat(1.f);
+        mi = dfloat(0.f);
+    } else if (J == 1) {
+        // 1 + c_1 theta: the product of the high parts split exactly (FMA), the cross
+        // terms added to its error
+        const float c1r = c.tcd_re_hi[k][1], c1rl = c.tcd_re_lo[k][1];
+        const float c1i = c.tcd_im_hi[k][1], c1il = c.tcd_im_lo[k][1];
+        const float pr = __fmul_rn(c1r, t), pi = __fmul_rn(c1i, t);
+        float er = __fmaf_rn(c1r, t, -pr), ei = __fmaf_rn(c1i, t, -pi);
+        er = __fmaf_rn(c1r, th.lo, __fmaf_rn(c1rl, t, er));
+        ei = __fmaf_rn(c1i, th.lo, __fmaf_rn(c1il, t, ei));
+        const dfloat h = fast_two_sum(1.f, pr);  // |pr| < 1
+        mr = fast_two_sum(h.hi, __fadd_rn(h.lo, __fadd_rn(er, tr)));
+        mi = fast_two_sum(pi, __fadd_rn(ei, ti));
+        return;
+    } else {
+        dfloat hr = dfloat(c.tcd_re_hi[k][J], c.tcd_re_lo[k][J]), hi = dfloat(c.tcd_im_hi[k][J], c.tcd_im_lo[k][J]);
+#pragma unroll 1
+        for (int j = J - 1; j >= 1; --j) {
+            hr = fma(hr, th, dfloat(c.tcd_re_hi[k][j], c.tcd_re_lo[k][j]));
+            hi = fma(hi, th, dfloat(c.tcd_im_hi[k][j], c.tcd_im_lo[k][j]));
+        }
+        mr = fma(hr, th, dfloat(1.f));
+        mi = hi * th;
+    }
+    if (D > J) {
+        mr = fast_two_sum(mr.hi, __fadd_rn(mr.lo, tr));
+        mi = fast_two_sum(mi.hi, __fadd_rn(mi.lo, ti));
+    }
+}
+
 // A Taylor degree known only at run time (warp-uniform): the double-float path, whose
 // Horner steps are long enough that a loop costs little and one code path per degree
 // would only grow the kernel.
 struct RtDeg {
     static constexpr int value = -1;
-    int d;
+    int d;  // degree
+    int J;  // head degree of taylor_split
 };
 
 // exp(-tau_k theta) by a Taylor polynomial of degree Dc (Horner, complex coefficients,
@@ -265,19 +365,7 @@ __device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real 
         }
     } else {
         const int D = dc.d;
-        Real ar = TermConsts<Real>::tc_re(c, k, D), ai = TermConsts<Real>::tc_im(c, k, D);
-#pragma unroll 1
-        for (int j = D - 1; j >= 1; --j) {
-            ar = fma(ar, th, TermConsts<Real>::tc_re(c, k, j));
-            ai = fma(ai, th, TermConsts<Real>::tc_im(c, k, j));
-        }
-        if (D > 0) {
-            mr = fma(ar, th, Real(1));
-            mi = ai * th;
-        } else {
-            mr = Real(1);
-            mi = Real(0);
-        }
+        taylor_split(c, k, D, dc.J, th, mr, mi);
         if (D == MaxDegree<Real>::value && theta_hw<Real>(th) > TermConsts<Real>::lim(c, k, D))
             cexp_term<Real>(c, k, th, mr, mi);
     }
@@ -288,7 +376,7 @@ __device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real 
 template <typename Real, typename Body>
 __device__ __forceinline__ void with_degree(int deg, Body&& body) {
     if constexpr (std::is_same<Real, dfloat>::value) {
-        body(RtDeg{deg});
+        body(RtDeg{deg & ((1 << kSplitShift) - 1), deg >> kSplitShift});
     } else {
         switch (deg) {
             case 0: body(std::integral_constant<int, 0>{}); break;
@@ -683,7 +771,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                     if constexpr (kF64) {
                         if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
                     }
-                    cfma<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+                    cfma_ra<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
                 }
             });
             multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
@@ -756,7 +844,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
-                cfma<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], Real(0), fr, fi);
+                cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
                 eval(r);
             }
         } else {
@@ -771,7 +859,7 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                     const bool tg = (tmask >> r) & 1u;
                     Real* slot = &s_al[pad<R>(i0 + r)];
                     const Real v = *slot;  // strength at a source, running value at a target
-                    cfma<Real>(mr, mi, fr, fi, tg ? Real(0) : v, Real(0), fr, fi);
+                    cfma_ra<Real>(mr, mi, fr, fi, tg ? Real(0) : v, fr, fi);
                     if (tg) {
                         if constexpr ((EV & 1) != 0) *slot = fma(Wr, fr, fma(-Wi, fi, v));
                         if constexpr ((EV & 2) != 0)
@@ -907,7 +995,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                 Real mr, mi;
                 mult_at(k, Dc, r, mr, mi);
                 // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
-                cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+                cfma_ra<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], br, bi);
             }
         });
         Real Mr, Mi;
@@ -959,7 +1047,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                 for (int r = R - 1; r >= 0; --r) {
                     Real mr, mi;
                     mult_at(k, Dc, r, mr, mi);
-                    cfma<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], Real(0), br, bi);
+                    cfma_ra<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], br, bi);
                     if ((tmask >> r) & 1u) {
                         if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
                         if constexpr ((EV & 2) != 0)
@@ -975,7 +1063,7 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                     const bool tg = (tmask >> r) & 1u;
                     Real* slot = &s_al[pad<R>(i0 + r)];
                     const Real v = *slot;
-                    cfma<Real>(mr, mi, br, bi, tg ? Real(0) : v, Real(0), br, bi);
+                    cfma_ra<Real>(mr, mi, br, bi, tg ? Real(0) : v, br, bi);
                     if (tg) {
                         if constexpr ((EV & 1) != 0) *slot = fma(Wr, br, fma(-Wi, bi, v));
                         if constexpr ((EV & 2) != 0)

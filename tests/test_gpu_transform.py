@@ -160,6 +160,33 @@ def test_f32x2_vs_direct(cuda, eps, delta):
     assert rel_inf(u[idx], ref, a) <= 2 * eps + 1e-13
 
 
+@pytest.mark.parametrize("delta", [1e-2, 1e-5])
+def test_f32x2_dense_vs_recurrence(cuda, delta):
+    """Dense points (|tau| theta below 2^-13 almost everywhere): the double-float
+    multipliers take the 1 - tau theta + FP32-tail form."""
+    x, y, a = inputs.uniform(1 << 20, 1 << 20, seed=41)
+    plan, tau, W = oracle_soe_plan(delta, 1e-10, precision="f32x2")
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= TOL_ARITH_DF
+
+
+@pytest.mark.parametrize("delta", [100.0, 10.0, 1.0, 1e-2, 1e-4, 1e-6])
+def test_f32x2_matches_fp64_path(cuda, delta):
+    """Double-float against the FP64 path on the same plan nodes: every split of the
+    double-float Taylor evaluation (head degree J = 1, 2, 3, ... as the gaps grow
+    relative to sqrt(delta)) must keep the multipliers at double-float accuracy.  The
+    bound is TOL_ARITH64 / 10 relative to sum |alpha| (double-float rounding, 2^-48 per
+    step, over up to P = 4e4 steps of a recurrence whose terms cancel as delta grows)."""
+    x, y, a = inputs.uniform(20000, 20000, seed=43)
+    n, tau, W, En = soe_cf.plan_soe(1e-10)
+    u64 = gpu_transform(fgt.Plan(delta, soe=(tau, W)), x, y, a)
+    udf = gpu_transform(fgt.Plan(delta, soe=(tau, W), precision="f32x2"), x, y, a)
+    err = rel_inf(udf, u64, a)
+    print("delta", delta, "f32x2 vs fp64 / sum|alpha|", err, "/ max|u|", np.max(np.abs(udf - u64)) / np.max(np.abs(u64)))
+    assert err <= TOL_ARITH64 / 10
+
+
 def test_f32x2_mixture_and_ties(cuda):
     """Clustered points (gaps across many binades) and exact ties / signed zeros."""
     for x, y, a, delta in [(*inputs.mixture(30000, 30000, seed=9), 1e-6), (*inputs.with_ties(5000, 4000, seed=3), 1e-2)]:

@@ -47,6 +47,9 @@ SIGNATURES = {
     "fgt1d_backward": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "fgt1d_sort_workspace_size": (_I, [_I64, _I64, _P]),
     "fgt1d_sort_merged": (_I, [_P, _I64, _P, _I64, _P, _P, _SZ, _P]),
+    "fgt1d_geometry_workspace_size": (_I, [_P, _I64, _I64, _P]),
+    "fgt1d_geometry_bind": (_I, [_P, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    "fgt1d_geometry_apply": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
     "fgt1d_plan_set_tile": (_I, [_P, _I]),
     "fgt1d_plan_get_tile": (_I, [_P, _P]),
     "fgt1d_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _I, _P, _P, _P]),

@@ -215,6 +215,33 @@ struct ItemSource {
     const double* delta = nullptr;
 };
 
+// Sweep arguments over the sorted keys and codes held in the workspace.
+SweepArgs sweep_args(const double* alpha, int64_t N, double* u, double* out2, char* ws, const Layout& L) {
+    SweepArgs w;
+    w.N = N;
+    w.items = reinterpret_cast<const Item*>(ws + L.items);
+    w.B = L.B;
+    w.total_tiles = reinterpret_cast<const int64_t*>(ws + L.header + 80);
+    w.max_tiles = L.max_tiles;
+    w.Ppad = L.Ppad;
+    w.keysA = reinterpret_cast<const uint64_t*>(ws + L.keysA);
+    w.keysB = reinterpret_cast<const uint64_t*>(ws + L.keysB);
+    w.valsA = reinterpret_cast<const uint32_t*>(ws + L.valsA);
+    w.valsB = reinterpret_cast<const uint32_t*>(ws + L.valsB);
+    w.plan = reinterpret_cast<const SortPlan*>(ws + L.header + 128);
+    w.alpha = alpha;
+    w.mult = L.mult ? reinterpret_cast<double2*>(ws + L.mult) : nullptr;
+    w.fwd = ws + L.fwd;
+    w.fwd2 = L.fwd2 ? ws + L.fwd2 : nullptr;
+    w.u = u;
+    w.out2 = out2;
+    w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
+    w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
+    w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
+    w.status = reinterpret_cast<uint32_t*>(ws + L.header);
+    return w;
+}
+
 // Sort + sweeps for targets x[M], sources y[N] with strengths alpha.  ev selects the
 // evaluation channels (1: values into u, 2: derivative into out2); coinc (may be null)
 // receives the per-target sums of coincident source strengths.
@@ -236,28 +263,7 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     e = launch_sort(sa, st);
     if (e == cudaSuccess) e = rec(1);
     if (e != cudaSuccess) return FGT1D_ECUDA;
-    SweepArgs w;
-    w.N = N;
-    w.items = items;
-    w.B = L.B;
-    w.total_tiles = total_tiles;
-    w.max_tiles = L.max_tiles;
-    w.Ppad = L.Ppad;
-    w.keysA = sa.keysA;
-    w.keysB = sa.keysB;
-    w.valsA = sa.valsA;
-    w.valsB = sa.valsB;
-    w.plan = sa.plan;
-    w.alpha = alpha;
-    w.mult = L.mult ? reinterpret_cast<double2*>(ws + L.mult) : nullptr;
-    w.fwd = ws + L.fwd;
-    w.fwd2 = L.fwd2 ? ws + L.fwd2 : nullptr;
-    w.u = u;
-    w.out2 = out2;
-    w.fdesc = reinterpret_cast<TileDesc*>(ws + L.fdesc);
-    w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
-    w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
-    w.status = status;
+    SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
@@ -489,6 +495,115 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
     SortArgs sa = sort_args(x, y, N, ws, L);
     if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
     return cuda_status(launch_copy_perm(sa, M + N, perm, st));
+}
+
+// ---- fixed geometry: bind once, apply many strength vectors ------------------------------
+namespace {
+
+constexpr size_t kTagOffset = 96;  // geometry tag in the workspace header
+
+// Identifies what a bound table depends on: sizes, delta and the nodes tau_k.
+uint64_t geometry_tag(const fgt1d_plan_s& p, int64_t M, int64_t N) {
+    uint64_t h = 0xcbf29ce484222325ull;  // FNV-1a over the raw bytes
+    auto mix = [&](const void* v, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(v);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 0x100000001b3ull;
+        }
+    };
+    const uint64_t magic = 0x6667743167656f6dull;
+    mix(&magic, 8);
+    mix(&M, 8);
+    mix(&N, 8);
+    mix(&p.n_e, sizeof(p.n_e));
+    mix(&p.delta, 8);
+    mix(p.tau_re, sizeof(double) * (size_t)p.n_e);
+    mix(p.tau_im, sizeof(double) * (size_t)p.n_e);
+    const int shape = shape_index(p, false);  // the table layout follows the tile shape
+    mix(&shape, sizeof(shape));
+    return h;
+}
+
+int geometry_checks(fgt1d_plan plan, int64_t M, int64_t N, void* ws, size_t ws_bytes, Layout& L) {
+    if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) return FGT1D_EUNSUPPORTED;
+    L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
+    if (M > 0 && N > 0) return ws_ok(ws, ws_bytes, L);
+    return FGT1D_OK;
+}
+
+}  // namespace
+
+extern "C" int fgt1d_geometry_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes) {
+    if (!bytes) return FGT1D_EINVAL;
+    Layout L;
+    int r = geometry_checks(plan, M, N, nullptr, 0, L);
+    if (r && r != FGT1D_EWORKSPACE) return r;
+    *bytes = L.total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_geometry_bind(fgt1d_plan plan, const double* x, int64_t M, const double* y, int64_t N,
+                                   void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    Layout L;
+    int r = geometry_checks(plan, M, N, workspace, ws_bytes, L);
+    if (r) return r;
+    if (M == 0 || N == 0) return FGT1D_OK;
+    if (!x || !y) return FGT1D_EINVAL;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_end, st);
+    int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
+    if (e == cudaSuccess)
+        e = launch_item_single(M, N, plan->delta, reinterpret_cast<Item*>(ws + L.items), total_tiles, st);
+    SortArgs sa = sort_args(x, y, N, ws, L);
+    if (e == cudaSuccess) e = launch_sort(sa, st);
+    SweepArgs w = sweep_args(nullptr, N, nullptr, nullptr, ws, L);
+    SweepConsts c = make_consts(*plan);
+    if (e == cudaSuccess) e = launch_fill_table(w, c, shape_index(*plan, false), st);
+    if (e == cudaSuccess)
+        e = launch_geometry_tag(reinterpret_cast<uint64_t*>(ws + L.header + kTagOffset), geometry_tag(*plan, M, N), st);
+    return cuda_status(e);
+}
+
+extern "C" int fgt1d_geometry_apply(fgt1d_plan plan, int64_t M, int64_t N, const double* alpha, double* u,
+                                    void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    Layout L;
+    int r = geometry_checks(plan, M, N, workspace, ws_bytes, L);
+    if (r) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M == 0) return FGT1D_OK;
+    if (!u) return FGT1D_EINVAL;
+    if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
+    if (!alpha) return FGT1D_EINVAL;
+    char* ws = static_cast<char*>(workspace);
+    const fgt1d_plan_s& p = *plan;
+    // per-apply state: sweep tile counters and look-back descriptors (the sorted points,
+    // the item table and the multiplier table stay)
+    cudaError_t e = cudaMemsetAsync(ws + L.header + 64, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.fdesc, 0, L.zero_end - L.fdesc, st);
+    int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.header);
+    if (e == cudaSuccess)
+        e = launch_geometry_check(reinterpret_cast<const uint64_t*>(ws + L.header + kTagOffset),
+                                  geometry_tag(p, M, N), total_tiles, status, st);
+    SweepArgs w = sweep_args(alpha, N, u, nullptr, ws, L);
+    w.reuse = 1;
+    SweepConsts c = make_consts(p);
+    if (e == cudaSuccess) e = launch_sweeps_f64(w, c, st, nullptr, 1, shape_index(p, false));
+    if (e == cudaSuccess && (p.flags & FGT1D_EXACT_SELF)) {
+        double* A = reinterpret_cast<double*>(ws + L.coinc);
+        e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
+        w.u = A;
+        w.reuse = 0;
+        if (e == cudaSuccess) e = launch_coincidence(w, c, st);
+        double s0 = 0.0;
+        for (int k = 0; k < p.n_e; ++k) s0 += p.w_re[k];
+        if (e == cudaSuccess) e = launch_axpy(A, 1.0 - s0, M, u, st);
+    }
+    return cuda_status(e);
 }
 
 extern "C" int fgt1d_plan_set_tile(fgt1d_plan plan, int threads) {

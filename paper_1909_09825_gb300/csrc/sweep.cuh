@@ -31,6 +31,9 @@
 // FP64 path (Real = double): every step in FP64.  The forward kernel stores the
 // multipliers (16 B per point and term): on GB300 one DFMA costs as much issue time
 // as 62 FFMAs, and reloading 16 B is cheaper than the 6-10 DFMAs of a multiplier.
+// Inside each 4096-point tile the table is thread-interleaved (tab_index): the
+// multiplier of a tile's point t R + r sits at slot r T + t, so that the R loads or
+// stores of a warp's 32 threads are each one contiguous 512-byte segment.
 // FP32 path (Real = float): gaps, multipliers and in-tile recurrences in FP32
 // complex; tile aggregates, span multipliers and carries in FP64.  Gaps come from the
 // integer difference of the sorted keys and FP64<->FP32 conversions are done with
@@ -515,6 +518,13 @@ struct SweepSmem {
 template <int R>
 __device__ __forceinline__ int pad(int i) { return i + i / R; }
 
+// Slot of merged point p in the thread-interleaved multiplier table of tile shape T x R.
+template <int T, int R>
+__device__ __forceinline__ int64_t tab_index(int64_t p) {
+    const int i = (int)(p & (kTile - 1));
+    return (p - i) + (int64_t)(i % R) * T + i / R;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real to_real(double v);
 template <>
@@ -712,26 +722,32 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
 
     const int i0 = tid * R;
     const double zprev = s_zprev, zend = s_z[pad<R>(nvalid - 1)];
+    // multipliers read from a bound geometry's table (FP64 only): no gaps needed
+    const bool reuse = kF64 && !CO && a.reuse;
     // gaps of my R points, warp-wide largest gap
     Real thr[R];
     uint32_t hw = 0;
+    if (!reuse) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = i0 + r;
-        Real t = 0;
-        if (i < nvalid && (i > 0 || !first))
-            t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], sc);
-        thr[r] = t;
-        hw = max(hw, theta_hw<Real>(t));
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r;
+            Real t = 0;
+            if (i < nvalid && (i > 0 || !first))
+                t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], sc);
+            thr[r] = t;
+            hw = max(hw, theta_hw<Real>(t));
+        }
+        hw = __reduce_max_sync(0xffffffffu, hw);
     }
-    hw = __reduce_max_sync(0xffffffffu, hw);
     Real thsp = 0;
     if (i0 < nvalid && (!first || i0 > 0))
         thsp = gap_real<Real>(i0 > 0 ? s_z[pad<R>(i0 - 1)] : zprev, s_z[pad<R>(min(i0 + R - 1, nvalid - 1))], sc);
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
+    if (!reuse) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) s_th[pad<R>(i0 + r)] = thr[r];
+        for (int r = 0; r < R; ++r) s_th[pad<R>(i0 + r)] = thr[r];
+    }
     uint32_t tmask = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) tmask |= ((s_tgt[(i0 + r) >> 5] >> ((i0 + r) & 31)) & 1u) << r;
@@ -761,19 +777,33 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
             Mr = thsp == Real(0) ? Real(1) : Real(0);
             Mi = 0;
         } else {
-            const int deg = taylor_degree<Real>(c, k, hw);
-            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + i0 : nullptr;
-            with_degree<Real>(deg, [&](auto Dc) {
+            // this thread's R multipliers are slots r T + tid of the tile (tab_index)
+            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
+            bool loaded = false;
+            if constexpr (kF64) {
+                if (reuse) {
 #pragma unroll 4
-                for (int r = 0; r < R; ++r) {
-                    Real mr, mi;
-                    taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
-                    if constexpr (kF64) {
-                        if (i0 + r < nvalid) mt[r] = make_double2((double)mr, (double)mi);
+                    for (int r = 0; r < R; ++r) {
+                        const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
+                        cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
                     }
-                    cfma_ra<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
+                    loaded = true;
                 }
-            });
+            }
+            if (!loaded) {
+                const int deg = taylor_degree<Real>(c, k, hw);
+                with_degree<Real>(deg, [&](auto Dc) {
+#pragma unroll 4
+                    for (int r = 0; r < R; ++r) {
+                        Real mr, mi;
+                        taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
+                        if constexpr (kF64) {
+                            if (i0 + r < nvalid) mt[r * T] = make_double2((double)mr, (double)mi);
+                        }
+                        cfma_ra<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
+                    }
+                });
+            }
             multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
         }
 #pragma unroll
@@ -840,10 +870,10 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
                 eval(r);
             }
         } else if constexpr (kF64) {
-            const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + i0;
+            const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + tid;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const double2 m = i0 + r < nvalid ? mt[r] : make_double2(1.0, 0.0);
+                const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
                 cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
                 eval(r);
             }
@@ -977,7 +1007,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
     auto mult_at = [&](int k, auto Dc, int r, Real& mr, Real& mi) {
         if constexpr (kF64) {
             const int64_t p = base + i0 + r + 1;
-            const double2 m = local + i0 + r + 1 < preal ? a.mult[(int64_t)k * a.Ppad + p] : make_double2(0.0, 0.0);
+            const double2 m =
+                local + i0 + r + 1 < preal ? a.mult[(int64_t)k * a.Ppad + tab_index<T, R>(p)] : make_double2(0.0, 0.0);
             mr = m.x;
             mi = m.y;
         } else {
@@ -1087,6 +1118,39 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
                 a.u[t] = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
             if constexpr ((EV & 2) != 0)
                 a.out2[t] = s * real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
+        }
+    }
+}
+
+// The multiplier table of a bound geometry (FP64): exp(-tau_k s (z_p - z_{p-1})) for
+// every real point p of every item (1 at an item's first point), the values the forward
+// sweep would store, at slot tab_index of the sweeps' tile shape sT x sR.  One block per
+// 4096-point tile; thread t fills slots t, t + T, ... (coalesced stores).
+template <int T>
+__global__ void __launch_bounds__(T) k_fill_table(const SweepArgs a, const SweepConsts c, int sT, int sR) {
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    if (tid == 0) s_item = tile < *a.total_tiles ? item_of_tile(a.items, a.B, tile) : -1;
+    __syncthreads();
+    if (s_item < 0) return;
+    const Item itm = a.items[s_item];
+    const int64_t base = tile * kTile, local = base - itm.start;
+    const int nvalid = (int)min((int64_t)kTile, itm.nsrc + itm.ntgt - local);
+    const uint64_t* __restrict__ keys = a.plan->final_buf == 1 ? a.keysB : a.keysA;
+    const double s = itm.s;
+    for (int j0 = 0; j0 < kTile; j0 += T) {
+        const int j = j0 + tid;             // table slot
+        const int i = (j % sT) * sR + j / sT;  // its point in the tile
+        double th = 0.0;
+        if (i < nvalid && (i > 0 || local > 0))
+            th = s * (key_coord(keys[base + i]) - key_coord(keys[base + i - 1]));
+        const uint32_t hw = __reduce_max_sync(0xffffffffu, theta_hw<double>(th));
+        for (int k = 0; k < c.n_e; ++k) {
+            double mr, mi;
+            with_degree<double>(taylor_degree<double>(c, k, hw),
+                                [&](auto Dc) { taylor<double>(c, k, Dc, th, mr, mi); });
+            if (i < nvalid) a.mult[(int64_t)k * a.Ppad + base + j] = make_double2(mr, mi);
         }
     }
 }

@@ -37,6 +37,30 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
     kf<<<(unsigned)a.max_tiles, kT64, smem, st>>>(a, c);
     return cudaGetLastError();
 }
+
+cudaError_t launch_fill_table(const SweepArgs& a, const SweepConsts& c, int shape, cudaStream_t st) {
+    const int sT = shape == 1 ? Shape<1>::T : Shape<0>::T, sR = shape == 1 ? Shape<1>::R : Shape<0>::R;
+    k_fill_table<256><<<(unsigned)a.max_tiles, 256, 0, st>>>(a, c, sT, sR);
+    return cudaGetLastError();
+}
+
+__global__ void k_geometry_check(const uint64_t* tag, uint64_t expect, int64_t* total_tiles, uint32_t* status) {
+    if (*tag != expect) {
+        *total_tiles = 0;
+        atomicOr(status, kStatusBadArg);
+    }
+}
+__global__ void k_geometry_tag(uint64_t* tag, uint64_t value) { *tag = value; }
+
+cudaError_t launch_geometry_check(const uint64_t* tag, uint64_t expect, int64_t* total_tiles, uint32_t* status,
+                                  cudaStream_t st) {
+    k_geometry_check<<<1, 1, 0, st>>>(tag, expect, total_tiles, status);
+    return cudaGetLastError();
+}
+cudaError_t launch_geometry_tag(uint64_t* tag, uint64_t value, cudaStream_t st) {
+    k_geometry_tag<<<1, 1, 0, st>>>(tag, value);
+    return cudaGetLastError();
+}
 #endif
 #elif FGT_SW_PREC == 1
 cudaError_t FGT_CAT(sweeps_f32_s, FGT_SW_SHAPE, _ne, FGT_SW_NE)(const SweepArgs& a, const SweepConsts& c,

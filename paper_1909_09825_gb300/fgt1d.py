@@ -276,6 +276,44 @@ def gauss_transform(x, y, alpha, delta, eps=1e-10, precision="fp64"):
     return GaussTransform.apply(x, y, alpha, dt, plan)
 
 
+class Geometry:
+    """Fixed targets x and sources y bound once (fgt1d_geometry_bind: sorted merged
+    points and the FP64 multiplier table kept on the device); apply() then evaluates
+    the transform for any strength vector without sorting or exponentials.  Owns its
+    workspace.  FP64 plans only."""
+
+    def __init__(self, plan, x, y, stream=None, sync_check=True):
+        _dev(x, "x"), _dev(y, "y")
+        self.plan, self.M, self.N = plan, x.numel(), y.numel()
+        b = ctypes.c_size_t()
+        check(lib().fgt1d_geometry_workspace_size(plan.handle, self.M, self.N, ctypes.byref(b)),
+              "geometry_workspace_size")
+        self.ws = torch.empty(max(int(b.value), 256), dtype=torch.uint8, device=x.device)
+        st = _stream_ptr(stream)
+        check(lib().fgt1d_geometry_bind(plan.handle, ctypes.c_void_p(x.data_ptr()), self.M,
+                                        ctypes.c_void_p(y.data_ptr()), self.N, ctypes.c_void_p(self.ws.data_ptr()),
+                                        self.ws.numel(), st), "geometry_bind")
+        if sync_check:
+            check(lib().fgt1d_check(ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), st), "geometry_bind (device)")
+
+    def apply(self, alpha, out=None, stream=None, sync_check=True):
+        """u = the transform of alpha (N,) at the bound points; returns u (M,)."""
+        _dev(alpha, "alpha")
+        if alpha.numel() != self.N:
+            raise ValueError("alpha must have N entries")
+        if out is None:
+            out = torch.empty(self.M, dtype=torch.float64, device=alpha.device)
+        _dev(out, "out")
+        st = _stream_ptr(stream)
+        check(lib().fgt1d_geometry_apply(self.plan.handle, self.M, self.N, ctypes.c_void_p(alpha.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(self.ws.data_ptr()),
+                                         self.ws.numel(), st), "geometry_apply")
+        if sync_check:
+            check(lib().fgt1d_check(ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), st),
+                  "geometry_apply (device)")
+        return out
+
+
 def transform_batched(plan, x_off, y_off, x, y, alpha, delta=None, out=None, workspace=None, stream=None,
                       sync_check=True):
     """B independent transforms in one pass (fgt1d_execute_batched).

@@ -111,6 +111,23 @@ def test_tile_shape_setting(L):
                             None) == _lib.FGT1D_EINVAL  # reps < 1
 
 
+def test_geometry_argument_errors(L):
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    b = ctypes.c_size_t()
+    p64 = fgt.Plan(1e-3, 1e-6)
+    assert L.fgt1d_geometry_workspace_size(p64.handle, 1000, 2000, ctypes.byref(b)) == _lib.FGT1D_OK
+    n = ctypes.c_size_t()
+    assert L.fgt1d_workspace_size(p64.handle, 1000, 2000, ctypes.byref(n)) == _lib.FGT1D_OK
+    assert b.value == n.value  # the bound state is the transform's workspace
+    p32 = fgt.Plan(1e-3, 1e-6, precision="fp32")
+    assert L.fgt1d_geometry_workspace_size(p32.handle, 1000, 2000, ctypes.byref(b)) == _lib.FGT1D_EUNSUPPORTED
+    assert L.fgt1d_geometry_workspace_size(p64.handle, -1, 2000, ctypes.byref(b)) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_geometry_bind(p64.handle, None, 10, None, 10, None, 0, None) == _lib.FGT1D_EWORKSPACE
+    assert L.fgt1d_geometry_apply(None, 10, 10, None, None, None, 0, None) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_geometry_apply(p64.handle, 0, 10, None, None, None, 0, None) == _lib.FGT1D_OK  # M = 0: no-op
+
+
 def test_workspace_size_and_bounds(L):
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import _lib

@@ -274,6 +274,7 @@ def main():
     extra = {}
     if not args.no_also:
         extra["geometry_reuse"] = geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args)
+        extra["identical_points"] = identical_points(X, A, dev, world, stream)
         extra["precision_split"] = precision_split(args, dev, world, P)
         extra["differentiation"] = differentiation(dev, world)
         extra["batched"] = batched(dev, world)
@@ -385,6 +386,32 @@ def geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args):
                                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                                "algorithmic_ops_per_unit": "unit = (merged point, term): 8 + 4 M/P FP64 ops",
                                "table_bytes_per_point": 2 * 16 * n_e}}
+
+
+def identical_points(X, A, dev, world, stream):
+    """Fig. 4.1's case (targets = sources, the shape of Table 5.1: uniform points,
+    delta = 1): the N = 2^26 headline targets with their strengths, one sort of N
+    points (fgt1d_execute_self), against the general path on (x, x) (2N merged points)."""
+    import torch
+    import paper_1909_09825_gb300 as fgt
+    N = X.numel()
+    out = []
+    U = torch.empty(N, dtype=torch.float64, device=dev)
+    A_ = A[:N]
+    for eps in (1e-6, 1e-10):
+        plan = fgt.Plan(1.0, eps)
+        ws = fgt.Workspace(dev)
+        ms_self = _event_time(lambda: fgt.transform_self(plan, X, A_, out=U, workspace=ws, sync_check=False), 3, 3,
+                              stream)
+        fgt.transform_self(plan, X, A_, out=U, workspace=ws)  # checks the device status
+        ms_gen = _event_time(lambda: fgt.transform(plan, X, X, A_, out=U, workspace=ws, sync_check=False), 3, 2,
+                             stream)
+        out.append({"eps": eps, "n_e": plan.n_e, "points_per_s": world * N / (ms_self * 1e-3), "ms": ms_self,
+                     "general_path_on_x_x_ms": ms_gen, "speedup": ms_gen / ms_self})
+        del ws
+        torch.cuda.empty_cache()
+    return {"workload": "N=2^%d uniform points as targets and sources, alpha ~ N(0,1), delta=1 "
+                        "(Table 5.1's shape), FP64" % int(np.log2(N)), "unit": "N points/s", "runs": out}
 
 
 def precision_split(args, dev, world, P_unused):

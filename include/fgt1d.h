@@ -153,6 +153,17 @@ int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const in
                           const double* alpha, int64_t N_total, double* u, void* workspace, size_t ws_bytes,
                           fgt1d_stream stream);
 
+/* Identical targets and sources (Fig. 4.1's case): u_i = sum_j G(x_i - x_j) alpha_j for
+ * the N points x (device), strengths alpha[N] and output u[N] (device, original order).
+ * The N points are sorted once (not 2N merged points); the forward state is inclusive
+ * and the backward state exclusive, so the self term and every coincident pair get
+ * S_n(0) as in Fig. 4.1.  Workspace: fgt1d_self_workspace_size.  FP64 plans without
+ * FGT1D_EXACT_SELF (others return FGT1D_EUNSUPPORTED).  N = 0 is a no-op.  Errors as
+ * fgt1d_execute. */
+int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes);
+int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,
+                       void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
 /* Fixed geometry (Sec. 5: when the transform is applied many times to fixed points
  * with different strength vectors, pre-sort the points and store every exponential in
  * a table).  fgt1d_geometry_bind sorts the merged points of targets x[M] and sources

@@ -233,6 +233,60 @@ int o3_recurrence(const double* x, int64_t M, const double* y, const double* alp
     return 0;
 }
 
+/* O3 for identical targets and sources (Fig. 4.1): sort the N points once (stable),
+ * forward pass h+_i = beta_i + e_{i-1} h+_{i-1} (inclusive), backward pass
+ * h-_i = e_i (beta_{i+1} + h-_{i+1}) (exclusive), u = Re sum_k W_k (h+ + h-), unpermute;
+ * beta is alpha in sorted order and e_i = exp(-t_k (x_{i+1} - x_i) / sqrt(delta)) for
+ * consecutive sorted points.  Returns 0 or the error of o3_sort_merged. */
+int o3_recurrence_self(const double* x, const double* alpha, int64_t N, double delta, int n_e, const double* tre,
+                       const double* tim, const double* wre, const double* wim, double* u) {
+    if (n_e < 1 || n_e > ORACLE_MAX_TERMS) return -3;
+    int64_t* perm = (int64_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+    double* hre = (double*)calloc((size_t)(N > 0 ? N : 1) * n_e, sizeof(double));
+    double* him = (double*)calloc((size_t)(N > 0 ? N : 1) * n_e, sizeof(double));
+    if (!perm || !hre || !him) { free(perm); free(hre); free(him); return -2; }
+    int rc = o3_sort_merged(NULL, 0, x, N, perm); /* the points as sources only */
+    if (rc) { free(perm); free(hre); free(him); return rc; }
+    const double sd = sqrt(delta);
+    double Fr[ORACLE_MAX_TERMS], Fi[ORACLE_MAX_TERMS];
+    for (int64_t i = 0; i < N; ++i) {
+        for (int k = 0; k < n_e; ++k) {
+            double nr = 0.0, ni = 0.0;
+            if (i > 0) {
+                double gap = x[perm[i]] - x[perm[i - 1]];
+                double mag = exp(-tre[k] * gap / sd), ang = tim[k] * gap / sd;
+                double er = mag * cos(ang), ei = -mag * sin(ang);
+                nr = er * Fr[k] - ei * Fi[k];
+                ni = er * Fi[k] + ei * Fr[k];
+            }
+            Fr[k] = nr + alpha[perm[i]];
+            Fi[k] = ni;
+            hre[i * n_e + k] = Fr[k];
+            him[i * n_e + k] = Fi[k];
+        }
+    }
+    double Br[ORACLE_MAX_TERMS], Bi[ORACLE_MAX_TERMS];
+    for (int k = 0; k < n_e; ++k) Br[k] = Bi[k] = 0.0;
+    for (int64_t i = N - 1; i >= 0; --i) {
+        if (i < N - 1) {
+            double gap = x[perm[i + 1]] - x[perm[i]];
+            for (int k = 0; k < n_e; ++k) {
+                double mag = exp(-tre[k] * gap / sd), ang = tim[k] * gap / sd;
+                double er = mag * cos(ang), ei = -mag * sin(ang);
+                double cr = Br[k] + alpha[perm[i + 1]], ci = Bi[k];
+                Br[k] = er * cr - ei * ci;
+                Bi[k] = er * ci + ei * cr;
+            }
+        }
+        double acc = 0.0;
+        for (int k = 0; k < n_e; ++k)
+            acc += wre[k] * (hre[i * n_e + k] + Br[k]) - wim[k] * (him[i * n_e + k] + Bi[k]);
+        u[perm[i]] = acc;
+    }
+    free(perm); free(hre); free(him);
+    return 0;
+}
+
 /* ---- direct gradients ------------------------------------------------------------------
  * L = sum_i g_i u_i.  For a kernel K(d), d = x_i - y_j:
  *   dL/dalpha_j = sum_i g_i K(d);  dL/dx_i = g_i sum_j alpha_j K'(d);

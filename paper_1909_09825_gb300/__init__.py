@@ -8,4 +8,5 @@ CUDA library libfgt1d.so (C ABI in include/fgt1d.h); this package only marshals
 arguments.  Import is lazy: the library is loaded on first use.
 """
 from .fgt1d import (Plan, soe_cf, transform, sort_merged, execute_host, Workspace, backward,  # noqa: F401
-                    GaussTransform, gauss_transform, transform_batched, Geometry)
+                    GaussTransform, gauss_transform, transform_batched, Geometry,
+                    transform_self)

@@ -47,6 +47,8 @@ SIGNATURES = {
     "fgt1d_backward": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "fgt1d_sort_workspace_size": (_I, [_I64, _I64, _P]),
     "fgt1d_sort_merged": (_I, [_P, _I64, _P, _I64, _P, _P, _SZ, _P]),
+    "fgt1d_self_workspace_size": (_I, [_P, _I64, _P]),
+    "fgt1d_execute_self": (_I, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
     "fgt1d_geometry_workspace_size": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_geometry_bind": (_I, [_P, _P, _I64, _P, _I64, _P, _SZ, _P]),
     "fgt1d_geometry_apply": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),

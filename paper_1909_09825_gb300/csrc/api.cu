@@ -247,7 +247,7 @@ SweepArgs sweep_args(const double* alpha, int64_t N, double* u, double* out2, ch
 // receives the per-target sums of coincident source strengths.
 int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
                  const ItemSource& src, double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L,
-                 cudaStream_t st, cudaEvent_t const* evs = nullptr) {
+                 cudaStream_t st, cudaEvent_t const* evs = nullptr, bool self = false) {
     auto rec = [&](int i) { return (evs && evs[i]) ? cudaEventRecord(evs[i], st) : cudaSuccess; };
     cudaError_t e = rec(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
@@ -264,6 +264,7 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     if (e == cudaSuccess) e = rec(1);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
+    w.self = self ? 1 : 0;
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
@@ -495,6 +496,28 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
     SortArgs sa = sort_args(x, y, N, ws, L);
     if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
     return cuda_status(launch_copy_perm(sa, M + N, perm, st));
+}
+
+// ---- identical targets and sources --------------------------------------------------------
+extern "C" int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes) {
+    if (!plan || !bytes || !sizes_ok(0, N)) return FGT1D_EINVAL;
+    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2 | FGT1D_EXACT_SELF)) return FGT1D_EUNSUPPORTED;
+    *bytes = make_layout(0, N, 1, plan->n_e, plan->flags, true, false).total;
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,
+                                  void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(0, N)) return FGT1D_EINVAL;
+    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2 | FGT1D_EXACT_SELF)) return FGT1D_EUNSUPPORTED;
+    if (N == 0) return FGT1D_OK;
+    if (!x || !alpha || !u) return FGT1D_EINVAL;
+    Layout L = make_layout(0, N, 1, plan->n_e, plan->flags, true, false);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    // the N points are merged once, as sources; the sweeps treat each as a target too
+    return run_pipeline(*plan, nullptr, 0, x, alpha, N, ItemSource(), u, nullptr, 1, nullptr,
+                        static_cast<char*>(workspace), L, static_cast<cudaStream_t>(stream), nullptr, true);
 }
 
 // ---- fixed geometry: bind once, apply many strength vectors ------------------------------

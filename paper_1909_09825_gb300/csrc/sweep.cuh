@@ -598,8 +598,12 @@ __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* _
             const int64_t p = base + i;
             z = key_coord(keys[p]);
             const uint32_t v = vals[p];
-            if ((int64_t)v < a.N) al = __ldg(&a.alpha[v]);
-            else tg = true;
+            if ((int64_t)v < a.N) {
+                al = __ldg(&a.alpha[v]);
+                tg = a.self != 0;  // identical targets and sources: every point is both
+            } else {
+                tg = true;
+            }
         }
         s_z[pad<R>(i)] = z;
         s_al[pad<R>(i)] = to_real<Real>(al);
@@ -1110,12 +1114,24 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         for (int r = 0; r < R; ++r) s_al[pad<R>(i0 + r)] = acc[r];
         __syncthreads();
     }
+    // identical targets and sources: the backward state includes the point's own
+    // strength, which the forward state already holds (eq. 4.4: the source at x_i belongs
+    // to h+); it is taken out once, Re sum_k W_k alpha_i = S_n(0) alpha_i
+    double s0 = 0.0;
+    if (a.self) {
+#pragma unroll
+        for (int k = 0; k < NE; ++k) s0 += c.w_re[k];
+    }
     for (int i = tid; i < nvalid; i += T) {
         if ((s_tgt[i >> 5] >> (i & 31)) & 1u) {
             const int64_t p = base + i;
-            const int64_t t = (int64_t)vals[p] - a.N;
-            if constexpr ((EV & 1) != 0)
-                a.u[t] = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
+            const uint32_t v = vals[p];
+            const int64_t t = (int64_t)v - (a.self ? 0 : a.N);
+            if constexpr ((EV & 1) != 0) {
+                double ui = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
+                if (a.self) ui -= s0 * __ldg(&a.alpha[v]);
+                a.u[t] = ui;
+            }
             if constexpr ((EV & 2) != 0)
                 a.out2[t] = s * real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
         }

@@ -276,6 +276,28 @@ def gauss_transform(x, y, alpha, delta, eps=1e-10, precision="fp64"):
     return GaussTransform.apply(x, y, alpha, dt, plan)
 
 
+def transform_self(plan, x, alpha, out=None, workspace=None, stream=None, sync_check=True):
+    """u_i = sum_j exp(-(x_i - x_j)^2 / (4 delta)) alpha_j with the N points as both
+    targets and sources (fgt1d_execute_self: one sort of N points; FP64 plans)."""
+    _dev(x, "x"), _dev(alpha, "alpha")
+    N = x.numel()
+    if alpha.numel() != N:
+        raise ValueError("alpha and x differ in length")
+    if out is None:
+        out = torch.empty(N, dtype=torch.float64, device=x.device)
+    _dev(out, "out")
+    b = ctypes.c_size_t()
+    check(lib().fgt1d_self_workspace_size(plan.handle, N, ctypes.byref(b)), "self_workspace_size")
+    ws = _workspace(workspace, x.device, b.value)
+    st = _stream_ptr(stream)
+    check(lib().fgt1d_execute_self(plan.handle, ctypes.c_void_p(x.data_ptr()), N, ctypes.c_void_p(alpha.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(), st),
+          "execute_self")
+    if sync_check:
+        check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "execute_self (device)")
+    return out
+
+
 class Geometry:
     """Fixed targets x and sources y bound once (fgt1d_geometry_bind: sorted merged
     points and the FP64 multiplier table kept on the device); apply() then evaluates

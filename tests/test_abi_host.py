@@ -128,6 +128,21 @@ def test_geometry_argument_errors(L):
     assert L.fgt1d_geometry_apply(p64.handle, 0, 10, None, None, None, 0, None) == _lib.FGT1D_OK  # M = 0: no-op
 
 
+def test_self_argument_errors(L):
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    b = ctypes.c_size_t()
+    assert L.fgt1d_self_workspace_size(fgt.Plan(1e-3, 1e-6).handle, 5000, ctypes.byref(b)) == _lib.FGT1D_OK
+    n = ctypes.c_size_t()
+    assert L.fgt1d_workspace_size(fgt.Plan(1e-3, 1e-6).handle, 0, 5000, ctypes.byref(n)) == _lib.FGT1D_OK
+    assert b.value == n.value  # N merged points, not 2N
+    for p in (fgt.Plan(1e-3, 1e-6, precision="fp32"), fgt.Plan(1e-3, 1e-6, precision="f32x2"),
+              fgt.Plan(1e-3, 1e-6, exact_self=True)):
+        assert L.fgt1d_self_workspace_size(p.handle, 5000, ctypes.byref(b)) == _lib.FGT1D_EUNSUPPORTED
+    assert L.fgt1d_execute_self(None, None, 10, None, None, None, 0, None) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_execute_self(fgt.Plan(1e-3, 1e-6).handle, None, 0, None, None, None, 0, None) == _lib.FGT1D_OK
+
+
 def test_workspace_size_and_bounds(L):
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import _lib

@@ -1,0 +1,70 @@
+"""Identical targets and sources (Fig. 4.1): fgt1d_execute_self against the oracle's
+one-sort recurrence, the brute-force SOE sum and the general merged transform."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1909_09825_gb300 as fgt
+from oracle import oracle, soe_cf
+from paper_1909_09825_gb300 import _lib, inputs
+
+from gpu_util import gpu_transform, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL_ARITH64 = 1e-12
+
+
+def _self(plan, x, a, dev):
+    T = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    return fgt.transform_self(plan, T(x), T(a)).cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [1, 2, 100, 4095, 4096, 4097, 30001])
+def test_self_vs_oracle(cuda, N):
+    x, _, _ = inputs.uniform(N, 1, seed=N)
+    a = np.random.default_rng(N + 1).standard_normal(N)
+    n, tau, W, En = soe_cf.plan_soe(1e-10)
+    for delta in (1.0, 1e-4):
+        plan = fgt.Plan(delta, soe=(tau, W))
+        u = _self(plan, x, a, cuda)
+        assert rel_inf(u, oracle.recurrence_self(x, a, delta, tau, W), a) <= TOL_ARITH64
+
+
+def test_self_ties_and_signed_zeros(cuda):
+    x, _, a = inputs.with_ties(6000, 6000, seed=4, n_distinct=40)
+    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    plan = fgt.Plan(1e-2, soe=(tau, W))
+    u = _self(plan, x, a, cuda)
+    assert rel_inf(u, oracle.recurrence_self(x, a, 1e-2, tau, W), a) <= TOL_ARITH64
+    idx = np.arange(0, 6000, 97)
+    assert rel_inf(u[idx], oracle.soe_direct(x[idx], x, a, 1e-2, tau, W), a) <= TOL_ARITH64
+
+
+def test_self_equals_merged_transform(cuda):
+    """The same sum through the general path with y = x (2N merged points)."""
+    x, _, a = inputs.mixture(50000, 1, seed=8)
+    a = np.random.default_rng(9).standard_normal(50000)
+    plan = fgt.Plan(1e-4, 1e-8)
+    u = _self(plan, x, a, cuda)
+    assert rel_inf(u, gpu_transform(plan, x, x, a), a) <= TOL_ARITH64
+
+
+def test_self_large_vs_direct(cuda):
+    """Table 5.1's workload shape (uniform points, delta = 1) at N = 2^22, sampled
+    targets against the direct Gauss sum."""
+    N = 1 << 22
+    x, _, _ = inputs.uniform(N, 1, seed=0)
+    a = np.random.default_rng(1).random(N)
+    plan = fgt.Plan(1.0, 1e-8)
+    u = _self(plan, x, a, cuda)
+    idx = np.random.default_rng(2).choice(N, 6, replace=False)
+    assert rel_inf(u[idx], oracle.direct(x[idx], x, a, 1.0, nthreads=0), a) <= 2e-8 + 1e-13
+
+
+def test_self_unsupported_plans(cuda):
+    x = torch.rand(100, dtype=torch.float64, device=cuda)
+    for plan in (fgt.Plan(1e-3, 1e-6, precision="fp32"), fgt.Plan(1e-3, 1e-6, exact_self=True)):
+        with pytest.raises(_lib.FGTError) as e:
+            fgt.transform_self(plan, x, x)
+        assert e.value.code == _lib.FGT1D_EUNSUPPORTED

@@ -65,6 +65,30 @@ def test_recurrence_equals_soe_direct_tiny(seed):
         assert np.max(np.abs(u3 - u2)) <= 1e-14 * np.abs(a).sum()
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_recurrence_self_equals_soe_direct_tiny(seed):
+    """Fig. 4.1's identical-points algorithm (one sort, inclusive forward and exclusive
+    backward pass) against the brute-force SOE sum with y = x, ties and signed zeros
+    included: every pair, the self pair too, gets the SOE kernel value."""
+    rng = np.random.default_rng(100 + seed)
+    N = int(rng.integers(1, 50))
+    vals = np.concatenate([[0.0, -0.0], rng.random(5)])
+    x = vals[rng.integers(0, 7, N)] if seed % 2 else rng.random(N)
+    a = rng.standard_normal(N)
+    tau, W, _ = soe_cf.cf_soe(10)
+    for delta in (1e-3, 0.3):
+        u = oracle.recurrence_self(x, a, delta, tau, W)
+        u2 = oracle.soe_direct(x, x, a, delta, tau, W)
+        assert np.max(np.abs(u - u2)) <= 1e-14 * np.abs(a).sum()
+
+
+def test_recurrence_self_one_point():
+    """N = 1: u = alpha S_n(0) = alpha Re sum_k W_k (the self weight of Fig. 4.1)."""
+    tau, W, _ = soe_cf.cf_soe(8)
+    u = oracle.recurrence_self(np.array([0.37]), np.array([2.0]), 1e-2, tau, W)
+    assert abs(u[0] - 2.0 * np.sum(W.real)) <= 1e-15
+
+
 def test_sort_matches_numpy_stable_argsort():
     x, y, _ = inputs.with_ties(5000, 4000, seed=2)
     perm = oracle.sort_merged(x, y)

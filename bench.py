@@ -171,6 +171,10 @@ def main():
     ap.add_argument("--log2", type=int, default=LOG2_M, help="log2 of M = N (default 26)")
     ap.add_argument("--no-also", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 128, 256],
+                    help="sweep tile threads; 0 = autotune each configuration (default)")
+    ap.add_argument("--precision", default=HEAD["precision"], choices=["fp64", "fp32", "f32x2"],
+                    help="precision of the headline configuration (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -203,7 +207,11 @@ def main():
     def timed(cfg, steps, warmup, profile=False):
         plan = fgt.Plan(cfg["delta"], cfg["eps"], precision=cfg["precision"])
         buf = ws.get(plan.workspace_size(M, N))
-        tune = plan.autotune(X, Y, A, reps=2, workspace=ws)  # untimed: picks the sweep tile shape
+        if args.tile:
+            plan.tile_threads = args.tile
+            tune = {}
+        else:
+            tune = plan.autotune(X, Y, A, reps=2, workspace=ws)  # untimed: picks the sweep tile shape
         for _ in range(warmup):
             fgt.transform(plan, X, Y, A, out=U, workspace=ws)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * steps)]
@@ -240,7 +248,7 @@ def main():
 
     gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     with ClockSampler(gpu_uuid) as clk:
-        plan, ms, stages = timed(HEAD, args.steps, args.warmup, profile=True)
+        plan, ms, stages = timed(dict(HEAD, precision=args.precision), args.steps, args.warmup, profile=True)
     clocks = clk.summary()
     value = world * P / (ms * 1e-3)
 
@@ -249,7 +257,9 @@ def main():
     fwd_ops = P * n_e * (C_CE + 4 + 2.0 * M / P) + 2 * P
     fwd_s = stages["fwd_sweep_ms"] * 1e-3
     achieved = 2 * fwd_ops / fwd_s / 1e12
-    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "k_sweep_fwd<double>", "achieved": achieved,
+    roofline = {"bound": "alu", "pipe": "fp64",
+                "kernel": "k_sweep_fwd<double, %d, %d, %d>" % (n_e, plan.tile_threads, 4096 // plan.tile_threads),
+                "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "152 SMs x 2 DFMA/clk/SM (probe) x 2 flop x 2070 MHz",
                 "algorithmic_ops_per_unit": "unit = (merged point, SOE term); C_ce=%d + 4 + 2 M/P FP64 ops, "
@@ -302,10 +312,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "f32x2": "f32x2"}[args.precision],
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD % (HEAD["delta"], HEAD["eps"]), "M": M, "N": N,
                            "delta": HEAD["delta"], "eps": HEAD["eps"], "n_e": plan.n_e, "E_n": plan.E_n,
-                           "precision": "fp64", "l2": "inputs (24 B/point, %.1f GB) larger than the 129 MB L2"
+                           "precision": args.precision, "tile_threads": plan.tile_threads, "l2": "inputs (24 B/point, %.1f GB) larger than the 129 MB L2"
                                                        % (24 * P / 2 ** 30 / 1.0),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "stages": stages, "error": head_err, "roofline": roofline, "cpu_baseline": cpu,
@@ -516,7 +527,8 @@ def _traffic_record(plan):
     rec = json.load(open(f))
     src = os.path.join(ROOT, "paper_1909_09825_gb300", "csrc", "sweep.cuh")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != h or rec.get("n_e") != plan.n_e:
+    if (rec.get("source_sha256_16") != h or rec.get("n_e") != plan.n_e or
+            rec.get("tile_threads") != plan.tile_threads or plan.precision != "fp64"):
         return None
     return rec["dram_bytes_per_point"]
 

@@ -159,6 +159,12 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
         // u (|tau| / Re tau) times the decay length, a few tens of ulps.
         const double at = std::hypot(p.tau_re[k], p.tau_im[k]);
         {
+            const double th = std::ldexp(1.0, -10) / at;
+            uint64_t b;
+            std::memcpy(&b, &th, 8);
+            c.theta_hyb_lim[k] = (uint32_t)(b >> 32) - 1u;
+        }
+        {
             double f = 1.0;
             c.theta_split_d[k][0] = 0;
             for (int J = 1; J <= kTaylorMax; ++J) {

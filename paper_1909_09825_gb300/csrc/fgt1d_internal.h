@@ -54,6 +54,9 @@ struct SweepConsts {
     // double-float: largest theta (float bits) for which the Taylor terms beyond degree J
     // can be summed in FP32, |tau_k theta|^(J+1) / (J+1)! <= 2^-28 (index J = 1..kTaylorMax)
     uint32_t theta_split_d[FGT1D_MAX_TERMS][kTaylorMax + 1];
+    // FP64: largest theta (high word) with |tau_k| theta <= 2^-10, below which the Taylor
+    // terms of degree >= 3 can be summed in FP32 (taylor_hybrid)
+    uint32_t theta_hyb_lim[FGT1D_MAX_TERMS];
 };
 
 }  // namespace fgt1d

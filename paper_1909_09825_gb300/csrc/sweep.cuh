@@ -31,7 +31,7 @@
 // FP64 path (Real = double): every step in FP64.  The forward kernel stores the
 // multipliers (16 B per point and term): on GB300 one DFMA costs as much issue time
 // as 62 FFMAs, and reloading 16 B is cheaper than the 6-10 DFMAs of a multiplier.
-// Inside each 4096-point tile the table is thread-interleaved (tab_index): the
+// Inside each 4096-point tile the table is thread-interleaved: the
 // multiplier of a tile's point t R + r sits at slot r T + t, so that the R loads or
 // stores of a warp's 32 threads are each one contiguous 512-byte segment.
 // FP32 path (Real = float): gaps, multipliers and in-tile recurrences in FP32
@@ -334,6 +334,27 @@ __device__ __forceinline__ void taylor_split<dfloat>(const SweepConsts& c, int k
     }
 }
 
+// FP64 exp(-tau_k theta) of degree D >= 3 for |tau_k| theta <= 2^-10 (warp-uniform): the
+// head 1 + c_1 theta + c_2 theta^2 in FP64 (Horner, 4 DFMA + 1 DADD), the tail
+// theta^3 sum_{j>=3} c_j theta^(j-3) in FP32 (Horner on the FP32 pipe, converted exactly).
+// The tail is below |tau theta|^3 / 6 <= 2^-32.6 and its FP32 rounding below (D + 2)
+// 2^-24 of it, so the result keeps the FP64 truncation rule's 2^-53 accuracy while the
+// FP64 pipe, the bound of these kernels, does 5 operations instead of 2 D.
+template <int D>
+__device__ __forceinline__ void taylor_hybrid(const SweepConsts& c, int k, double th, double& mr, double& mi) {
+    const float t = f64_to_f32(th);
+    float ar = c.tcf_re[k][D], ai = c.tcf_im[k][D];
+#pragma unroll
+    for (int j = D - 1; j >= 3; --j) {
+        ar = __fmaf_rn(ar, t, c.tcf_re[k][j]);
+        ai = __fmaf_rn(ai, t, c.tcf_im[k][j]);
+    }
+    const float t3 = __fmul_rn(__fmul_rn(t, t), t);
+    const double tr = f32_to_f64(__fmul_rn(ar, t3)), ti = f32_to_f64(__fmul_rn(ai, t3));
+    mr = fma(fma(c.tc_re[k][2], th, c.tc_re[k][1]), th, 1.0) + tr;
+    mi = fma(fma(c.tc_im[k][2], th, c.tc_im[k][1]), th, ti);
+}
+
 // A Taylor degree known only at run time (warp-uniform): the double-float path, whose
 // Horner steps are long enough that a loop costs little and one code path per degree
 // would only grow the kernel.
@@ -347,7 +368,14 @@ struct RtDeg {
 // real theta).  At the largest degree, points beyond its threshold fall back to
 // exp/sincos; below it the warp-uniform degree already covers every point.
 template <typename Real, typename Dc>
-__device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real th, Real& mr, Real& mi) {
+__device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real th, Real& mr, Real& mi,
+                                       bool hybrid = false) {
+    if constexpr (Dc::value >= 3 && std::is_same<Real, double>::value) {
+        if (hybrid) {
+            taylor_hybrid<Dc::value>(c, k, th, mr, mi);
+            return;
+        }
+    }
     if constexpr (Dc::value >= 0) {
         constexpr int D = Dc::value;
         if constexpr (D == 0) {
@@ -515,15 +543,33 @@ struct SweepSmem {
     static constexpr size_t bytes = scan_off + sizeof(Real) * 4 * NE * T;
 };
 
+// Terms per group.  The value-channel sweeps run their terms in equal groups, each
+// with its own phases A-C, when the scan region of all NE terms would push the tile's
+// shared memory past the occupancy target (two resident tiles per SM for 8-byte reals,
+// three for FP32); the derivative channel keeps one group, since its accumulators live
+// over the gaps that every phase A reads.
+template <typename Real, int NE, int T, int R, int EV, bool CO>
+struct SweepGroup {
+    static constexpr size_t kBudget = sizeof(Real) == 8 ? 110 * 1024 : 72 * 1024;
+    static constexpr int pick() {
+        if (EV != 1 || CO) return NE;
+        for (int G = 1; G <= NE; ++G) {
+            const int n = (NE + G - 1) / G;
+            if (SweepSmem<Real, 1, T, R>::scan_off + sizeof(Real) * 4 * (size_t)n * T <= kBudget) return n;
+        }
+        return 1;
+    }
+    static constexpr int NG = pick();
+};
+
+// Resident tiles per SM that the shared-memory footprint allows (8-byte reals: two;
+// FP32: three), given to the register allocator as the occupancy target.
+template <typename Real>
+struct SweepMinBlocks { static constexpr int value = sizeof(Real) == 8 ? 2 : 3; };
+
 template <int R>
 __device__ __forceinline__ int pad(int i) { return i + i / R; }
 
-// Slot of merged point p in the thread-interleaved multiplier table of tile shape T x R.
-template <int T, int R>
-__device__ __forceinline__ int64_t tab_index(int64_t p) {
-    const int i = (int)(p & (kTile - 1));
-    return (p - i) + (int64_t)(i % R) * T + i / R;
-}
 
 template <typename Real>
 __device__ __forceinline__ Real to_real(double v);
@@ -681,13 +727,15 @@ __device__ __forceinline__ dfloat shfl_down<dfloat>(dfloat v, int o) { return df
 // (NE = 1, multiplier 1 on zero gaps and 0 otherwise, unit weight; the per-target sums
 // are written straight to a.u), used by the gradients.
 template <typename Real, int NE, int T, int R, int EV, bool CO>
-__global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepConsts c) {
-    using SM = SweepSmem<Real, NE, T, R>;
+__global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(const SweepArgs a, const SweepConsts c) {
+    constexpr int NG = SweepGroup<Real, NE, T, R, EV, CO>::NG;
+    using SM = SweepSmem<Real, NG, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
     constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
+    static_assert((EV & 2) == 0 || NG == NE, "the derivative channel runs its terms as one group");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
     Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gaps, written over s_z
@@ -769,138 +817,154 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
         s_M[k][1] = mi;
     }
 
-    // phase A: per term, thread aggregates and the warp scan
-#pragma unroll 1
-    for (int k = 0; k < NE; ++k) {
-        Real fr = 0, fi = 0;
-        Real Mr, Mi;
-        if constexpr (CO) {
-#pragma unroll 4
-            for (int r = 0; r < R; ++r)
-                fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
-            Mr = thsp == Real(0) ? Real(1) : Real(0);
-            Mi = 0;
-        } else {
-            // this thread's R multipliers are slots r T + tid of the tile (tab_index)
-            double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
-            bool loaded = false;
-            if constexpr (kF64) {
-                if (reuse) {
-#pragma unroll 4
-                    for (int r = 0; r < R; ++r) {
-                        const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
-                        cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
-                    }
-                    loaded = true;
-                }
-            }
-            if (!loaded) {
-                const int deg = taylor_degree<Real>(c, k, hw);
-                with_degree<Real>(deg, [&](auto Dc) {
-#pragma unroll 4
-                    for (int r = 0; r < R; ++r) {
-                        Real mr, mi;
-                        taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
-                        if constexpr (kF64) {
-                            if (i0 + r < nvalid) mt[r * T] = make_double2((double)mr, (double)mi);
-                        }
-                        cfma_ra<Real>(mr, mi, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
-                    }
-                });
-            }
-            multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Real Mor = shfl_up<Real>(Mr, o), Moi = shfl_up<Real>(Mi, o);
-            Real For = shfl_up<Real>(fr, o), Foi = shfl_up<Real>(fi, o);
-            if (lane >= o) {
-                cfma<Real>(Mr, Mi, For, Foi, fr, fi, fr, fi);
-                cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
-            }
-        }
-        Real Mxr = shfl_up<Real>(Mr, 1), Mxi = shfl_up<Real>(Mi, 1);
-        Real Fxr = shfl_up<Real>(fr, 1), Fxi = shfl_up<Real>(fi, 1);
-        if (lane == 0) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
-        Real* sc = s_scan + (size_t)k * 4 * T;
-        sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
-        if (lane == 31) {
-            s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
-            s_w[k][w][2] = real_to_f64<Real>(fr); s_w[k][w][3] = real_to_f64<Real>(fi);
-        }
-    }
-    __syncthreads();
-    // phase B: one lane per term joins the warps and the tiles
-    for (int k = w; k < NE; k += NW)
-        tile_combine<NE, NW>(a, a.fdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, -1, first, !first ? s_M[k][0] : 1.0,
-                             !first ? s_M[k][1] : 0.0, s_w, s_win, k);
-    __syncthreads();
-    // phase C: apply the carries, final pass, evaluation at targets.  The value channel
-    // accumulates in registers on the table path (FP64) and in the targets' strength
-    // slots otherwise; the derivative channel in shared memory (over the coordinates /
-    // gaps, which the FP64 path no longer needs and the FP32 path keeps in the first
-    // half of the region).
+    // Accumulators of phase C.  The value channel accumulates in registers on the table
+    // path (FP64) and in the targets' strength slots otherwise; the derivative channel in
+    // shared memory (over the coordinates / gaps, which the FP64 path no longer needs and
+    // the FP32 path keeps in the first half of the region).
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
     Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
-    if constexpr ((EV & 2) != 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
-    }
+    // strength of point r in phase A: a target slot holds a running value once an earlier
+    // group's phase C has passed (recomputed-multiplier paths)
+    auto strength = [&](int r) {
+        if constexpr (!kF64) {
+            if ((tmask >> r) & 1u) return Real(0);
+        }
+        return s_al[pad<R>(i0 + r)];
+    };
+    // the terms run in groups of NG (SweepGroup); one group unless the scan region of all
+    // NE terms would not fit the occupancy target
+    for (int g0 = 0; g0 < NE; g0 += NG) {
+        const int g1 = min(NE, g0 + NG);
+        if (g0 > 0) __syncthreads();  // the previous group's phase C has read s_scan
+        // phase A: per term, thread aggregates and the warp scan
 #pragma unroll 1
-    for (int k = 0; k < NE; ++k) {
-        const Real* sc = s_scan + (size_t)k * 4 * T;
-        Real fr, fi;
-        cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
-                   sc[2 * T + tid], sc[3 * T + tid], fr, fi);
-        const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
-        const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
-        auto eval = [&](int r) {
-            if ((tmask >> r) & 1u) {
-                if constexpr (CO) {
-                    acc[r] += fr;
-                } else {
-                    if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
-                    if constexpr ((EV & 2) != 0)
-                        s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+        for (int k = g0; k < g1; ++k) {
+            Real fr = 0, fi = 0;
+            Real Mr, Mi;
+            if constexpr (CO) {
+#pragma unroll 4
+                for (int r = 0; r < R; ++r)
+                    fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
+                Mr = thsp == Real(0) ? Real(1) : Real(0);
+                Mi = 0;
+            } else {
+                // this thread's R multipliers are slots r T + tid of the tile (interleaved table)
+                double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
+                bool loaded = false;
+                if constexpr (kF64) {
+                    if (reuse) {
+#pragma unroll 4
+                        for (int r = 0; r < R; ++r) {
+                            const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
+                            cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
+                        }
+                        loaded = true;
+                    }
+                }
+                if (!loaded) {
+                    const int deg = taylor_degree<Real>(c, k, hw);
+                    const bool hyb = kF64 && hw <= c.theta_hyb_lim[k];
+                    with_degree<Real>(deg, [&](auto Dc) {
+#pragma unroll 4
+                        for (int r = 0; r < R; ++r) {
+                            Real mr, mi;
+                            taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi, hyb);
+                            if constexpr (kF64) {
+                                if (i0 + r < nvalid) mt[r * T] = make_double2((double)mr, (double)mi);
+                            }
+                            cfma_ra<Real>(mr, mi, fr, fi, strength(r), fr, fi);
+                        }
+                    });
+                }
+                multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                Real Mor = shfl_up<Real>(Mr, o), Moi = shfl_up<Real>(Mi, o);
+                Real For = shfl_up<Real>(fr, o), Foi = shfl_up<Real>(fi, o);
+                if (lane >= o) {
+                    cfma<Real>(Mr, Mi, For, Foi, fr, fi, fr, fi);
+                    cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
                 }
             }
-        };
-        if constexpr (CO) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
-                eval(r);
+            Real Mxr = shfl_up<Real>(Mr, 1), Mxi = shfl_up<Real>(Mi, 1);
+            Real Fxr = shfl_up<Real>(fr, 1), Fxi = shfl_up<Real>(fi, 1);
+            if (lane == 0) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
+            Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+            sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
+            if (lane == 31) {
+                s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+                s_w[k][w][2] = real_to_f64<Real>(fr); s_w[k][w][3] = real_to_f64<Real>(fi);
             }
-        } else if constexpr (kF64) {
-            const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + tid;
+        }
+        __syncthreads();
+        // phase B: one lane per term joins the warps and the tiles
+        for (int k = g0 + w; k < g1; k += NW)
+            tile_combine<NE, NW>(a, a.fdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, -1, first, !first ? s_M[k][0] : 1.0,
+                                 !first ? s_M[k][1] : 0.0, s_w, s_win, k);
+        __syncthreads();
+        // phase C: apply the carries, final pass, evaluation at targets.  The derivative
+        // accumulators go over the gaps, which phase A has finished with (one group)
+        if constexpr ((EV & 2) != 0) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
-                cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
-                eval(r);
-            }
-        } else {
-            // recomputed multipliers: the value channel accumulates in the targets' own
-            // (zero) strength slots, so the loop needs no register array and is only
-            // partly unrolled (smaller code per Taylor degree)
-            with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
-#pragma unroll kUnrollC
-                for (int r = 0; r < R; ++r) {
-                    Real mr, mi;
-                    taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
-                    const bool tg = (tmask >> r) & 1u;
-                    Real* slot = &s_al[pad<R>(i0 + r)];
-                    const Real v = *slot;  // strength at a source, running value at a target
-                    cfma_ra<Real>(mr, mi, fr, fi, tg ? Real(0) : v, fr, fi);
-                    if (tg) {
-                        if constexpr ((EV & 1) != 0) *slot = fma(Wr, fr, fma(-Wi, fi, v));
+            for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
+        }
+#pragma unroll 1
+        for (int k = g0; k < g1; ++k) {
+            const Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+            Real fr, fi;
+            cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                       sc[2 * T + tid], sc[3 * T + tid], fr, fi);
+            const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
+            const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
+            auto eval = [&](int r) {
+                if ((tmask >> r) & 1u) {
+                    if constexpr (CO) {
+                        acc[r] += fr;
+                    } else {
+                        if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, fr, fma(-Wi, fi, acc[r]));
                         if constexpr ((EV & 2) != 0)
                             s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
                     }
                 }
-            });
+            };
+            if constexpr (CO) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    fr = (s_th[pad<R>(i0 + r)] == Real(0) ? fr : Real(0)) + s_al[pad<R>(i0 + r)];
+                    eval(r);
+                }
+            } else if constexpr (kF64) {
+                const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + tid;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
+                    cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
+                    eval(r);
+                }
+            } else {
+                // recomputed multipliers: the value channel accumulates in the targets' own
+                // (zero) strength slots, so the loop needs no register array and is only
+                // partly unrolled (smaller code per Taylor degree)
+                with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
+#pragma unroll kUnrollC
+                    for (int r = 0; r < R; ++r) {
+                        Real mr, mi;
+                        taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
+                        const bool tg = (tmask >> r) & 1u;
+                        Real* slot = &s_al[pad<R>(i0 + r)];
+                        const Real v = *slot;  // strength at a source, running value at a target
+                        cfma_ra<Real>(mr, mi, fr, fi, tg ? Real(0) : v, fr, fi);
+                        if (tg) {
+                            if constexpr ((EV & 1) != 0) *slot = fma(Wr, fr, fma(-Wi, fi, v));
+                            if constexpr ((EV & 2) != 0)
+                                s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+                        }
+                    }
+                });
+            }
         }
     }
     // outputs, written coalesced through shared memory (values staged over s_al)
@@ -922,13 +986,15 @@ __global__ void __launch_bounds__(T) k_sweep_fwd(const SweepArgs a, const SweepC
 }
 
 template <typename Real, int NE, int T, int R, int EV>
-__global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepConsts c) {
-    using SM = SweepSmem<Real, NE, T, R>;
+__global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(const SweepArgs a, const SweepConsts c) {
+    constexpr int NG = SweepGroup<Real, NE, T, R, EV, false>::NG;
+    using SM = SweepSmem<Real, NG, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
     constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
     constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
+    static_assert((EV & 2) == 0 || NG == NE, "the derivative channel runs its terms as one group");
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_z = reinterpret_cast<double*>(smem + SM::z_off);
     Real* s_th = reinterpret_cast<Real*>(smem + SM::z_off);  // gap between points i and i+1, over s_z
@@ -1008,11 +1074,15 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
 
     // multiplier between points i0+r and i0+r+1 (stored table, or a Taylor polynomial
     // of compile-time degree D on the FP32 path)
+    // this thread's slots in the interleaved table start at base + tid; the multiplier of
+    // point i0 + r + 1 is at offset (r + 1) T, or for r = R - 1 at the next thread's first
+    // slot (+1), which for the last thread is the next tile's slot 0
+    const int64_t next_off = tid + 1 < T ? 1 : (int64_t)TILE - tid;
     auto mult_at = [&](int k, auto Dc, int r, Real& mr, Real& mi) {
         if constexpr (kF64) {
-            const int64_t p = base + i0 + r + 1;
-            const double2 m =
-                local + i0 + r + 1 < preal ? a.mult[(int64_t)k * a.Ppad + tab_index<T, R>(p)] : make_double2(0.0, 0.0);
+            const double2* mt = a.mult + (int64_t)k * a.Ppad + base + tid;
+            const double2 m = local + i0 + r + 1 < preal ? mt[r + 1 < R ? (int64_t)(r + 1) * T : next_off]
+                                                         : make_double2(0.0, 0.0);
             mr = m.x;
             mi = m.y;
         } else {
@@ -1020,93 +1090,106 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
         }
     };
 
-#pragma unroll 1
-    for (int k = 0; k < NE; ++k) {
-        const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
-        Real br = 0, bi = 0;
-        with_degree<Real>(deg, [&](auto Dc) {
-#pragma unroll 4
-            for (int r = R - 1; r >= 0; --r) {
-                Real mr, mi;
-                mult_at(k, Dc, r, mr, mi);
-                // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
-                cfma_ra<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], br, bi);
-            }
-        });
-        Real Mr, Mi;
-        multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);
-            Real For = shfl_down<Real>(br, o), Foi = shfl_down<Real>(bi, o);
-            if (lane + o < 32) {
-                cfma<Real>(Mr, Mi, For, Foi, br, bi, br, bi);
-                cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
-            }
-        }
-        Real Mxr = shfl_down<Real>(Mr, 1), Mxi = shfl_down<Real>(Mi, 1);
-        Real Fxr = shfl_down<Real>(br, 1), Fxi = shfl_down<Real>(bi, 1);
-        if (lane == 31) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
-        Real* sc = s_scan + (size_t)k * 4 * T;
-        sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
-        if (lane == 0) {
-            s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
-            s_w[k][w][2] = real_to_f64<Real>(br); s_w[k][w][3] = real_to_f64<Real>(bi);
-        }
-    }
-    __syncthreads();
-    for (int k = w; k < NE; k += NW)
-        tile_combine<NE, NW>(a, a.bdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, +1, !has_next,
-                             has_next ? s_M[k][0] : 1.0, has_next ? s_M[k][1] : 0.0, s_w, s_win, k);
-    __syncthreads();
     Real acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
     Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
-    if constexpr ((EV & 2) != 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
-    }
+    // strength of point r in phase A: a target slot holds a running value once an earlier
+    // group's phase C has passed (recomputed-multiplier paths)
+    auto strength = [&](int r) {
+        if constexpr (!kF64) {
+            if ((tmask >> r) & 1u) return Real(0);
+        }
+        return s_al[pad<R>(i0 + r)];
+    };
+    // the terms run in groups of NG (SweepGroup), as in the forward sweep
+    for (int g0 = 0; g0 < NE; g0 += NG) {
+        const int g1 = min(NE, g0 + NG);
+        if (g0 > 0) __syncthreads();  // the previous group's phase C has read s_scan
 #pragma unroll 1
-    for (int k = 0; k < NE; ++k) {
-        const Real* sc = s_scan + (size_t)k * 4 * T;
-        Real br, bi;  // state at the first point of the next thread
-        cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
-                   sc[2 * T + tid], sc[3 * T + tid], br, bi);
-        const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
-        const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
-        const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
-        with_degree<Real>(deg, [&](auto Dc) {
-            if constexpr (kF64) {
-#pragma unroll
+        for (int k = g0; k < g1; ++k) {
+            const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+            Real br = 0, bi = 0;
+            with_degree<Real>(deg, [&](auto Dc) {
+#pragma unroll 4
                 for (int r = R - 1; r >= 0; --r) {
                     Real mr, mi;
                     mult_at(k, Dc, r, mr, mi);
-                    cfma_ra<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], br, bi);
-                    if ((tmask >> r) & 1u) {
-                        if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
-                        if constexpr ((EV & 2) != 0)
-                            s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
-                    }
+                    // b_r = m_{r+1} b_{r+1} + alpha_r, with b_R (the next thread's state) = 0
+                    cfma_ra<Real>(mr, mi, br, bi, strength(r), br, bi);
                 }
-            } else {
-                // as in the forward sweep: values accumulate in the targets' strength slots
-#pragma unroll kUnrollC
-                for (int r = R - 1; r >= 0; --r) {
-                    Real mr, mi;
-                    mult_at(k, Dc, r, mr, mi);
-                    const bool tg = (tmask >> r) & 1u;
-                    Real* slot = &s_al[pad<R>(i0 + r)];
-                    const Real v = *slot;
-                    cfma_ra<Real>(mr, mi, br, bi, tg ? Real(0) : v, br, bi);
-                    if (tg) {
-                        if constexpr ((EV & 1) != 0) *slot = fma(Wr, br, fma(-Wi, bi, v));
-                        if constexpr ((EV & 2) != 0)
-                            s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
-                    }
+            });
+            Real Mr, Mi;
+            multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);
+                Real For = shfl_down<Real>(br, o), Foi = shfl_down<Real>(bi, o);
+                if (lane + o < 32) {
+                    cfma<Real>(Mr, Mi, For, Foi, br, bi, br, bi);
+                    cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
                 }
             }
-        });
+            Real Mxr = shfl_down<Real>(Mr, 1), Mxi = shfl_down<Real>(Mi, 1);
+            Real Fxr = shfl_down<Real>(br, 1), Fxi = shfl_down<Real>(bi, 1);
+            if (lane == 31) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
+            Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+            sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
+            if (lane == 0) {
+                s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+                s_w[k][w][2] = real_to_f64<Real>(br); s_w[k][w][3] = real_to_f64<Real>(bi);
+            }
+        }
+        __syncthreads();
+        for (int k = g0 + w; k < g1; k += NW)
+            tile_combine<NE, NW>(a, a.bdesc, tile, itm.tile0, itm.tile0 + itm.ntiles, +1, !has_next,
+                                 has_next ? s_M[k][0] : 1.0, has_next ? s_M[k][1] : 0.0, s_w, s_win, k);
+        __syncthreads();
+        if constexpr ((EV & 2) != 0) {  // derivative accumulators (one group)
+#pragma unroll
+            for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = 0;
+        }
+#pragma unroll 1
+        for (int k = g0; k < g1; ++k) {
+            const Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+            Real br, bi;  // state at the first point of the next thread
+            cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                       sc[2 * T + tid], sc[3 * T + tid], br, bi);
+            const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
+            const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
+            const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+            with_degree<Real>(deg, [&](auto Dc) {
+                if constexpr (kF64) {
+#pragma unroll
+                    for (int r = R - 1; r >= 0; --r) {
+                        Real mr, mi;
+                        mult_at(k, Dc, r, mr, mi);
+                        cfma_ra<Real>(mr, mi, br, bi, s_al[pad<R>(i0 + r)], br, bi);
+                        if ((tmask >> r) & 1u) {
+                            if constexpr ((EV & 1) != 0) acc[r] = fma(Wr, br, fma(-Wi, bi, acc[r]));
+                            if constexpr ((EV & 2) != 0)
+                                s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                        }
+                    }
+                } else {
+                    // as in the forward sweep: values accumulate in the targets' strength slots
+#pragma unroll kUnrollC
+                    for (int r = R - 1; r >= 0; --r) {
+                        Real mr, mi;
+                        mult_at(k, Dc, r, mr, mi);
+                        const bool tg = (tmask >> r) & 1u;
+                        Real* slot = &s_al[pad<R>(i0 + r)];
+                        const Real v = *slot;
+                        cfma_ra<Real>(mr, mi, br, bi, tg ? Real(0) : v, br, bi);
+                        if (tg) {
+                            if constexpr ((EV & 1) != 0) *slot = fma(Wr, br, fma(-Wi, bi, v));
+                            if constexpr ((EV & 2) != 0)
+                                s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                        }
+                    }
+                }
+            });
+        }
     }
     __syncthreads();
     if constexpr (kF64) {
@@ -1140,7 +1223,8 @@ __global__ void __launch_bounds__(T) k_sweep_bwd(const SweepArgs a, const SweepC
 
 // The multiplier table of a bound geometry (FP64): exp(-tau_k s (z_p - z_{p-1})) for
 // every real point p of every item (1 at an item's first point), the values the forward
-// sweep would store, at slot tab_index of the sweeps' tile shape sT x sR.  One block per
+// sweep would store, at the interleaved slot (i % sR) sT + i / sR of tile point i for
+// the sweeps' tile shape sT x sR.  One block per
 // 4096-point tile; thread t fills slots t, t + T, ... (coalesced stores).
 template <int T>
 __global__ void __launch_bounds__(T) k_fill_table(const SweepArgs a, const SweepConsts c, int sT, int sR) {
@@ -1164,8 +1248,9 @@ __global__ void __launch_bounds__(T) k_fill_table(const SweepArgs a, const Sweep
         const uint32_t hw = __reduce_max_sync(0xffffffffu, theta_hw<double>(th));
         for (int k = 0; k < c.n_e; ++k) {
             double mr, mi;
+            const bool hyb = hw <= c.theta_hyb_lim[k];
             with_degree<double>(taylor_degree<double>(c, k, hw),
-                                [&](auto Dc) { taylor<double>(c, k, Dc, th, mr, mi); });
+                                [&](auto Dc) { taylor<double>(c, k, Dc, th, mr, mi, hyb); });
             if (i < nvalid) a.mult[(int64_t)k * a.Ppad + base + j] = make_double2(mr, mi);
         }
     }

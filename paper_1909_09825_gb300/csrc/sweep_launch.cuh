@@ -7,7 +7,7 @@ namespace fgt1d {
 
 template <typename Real, int T, int R, int EV, int NE>
 cudaError_t run_sweep_pair(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid) {
-    const size_t smem = SweepSmem<Real, NE, T, R>::bytes;
+    const size_t smem = SweepSmem<Real, SweepGroup<Real, NE, T, R, EV, false>::NG, T, R>::bytes;
     auto kf = k_sweep_fwd<Real, NE, T, R, EV, false>;
     auto kb = k_sweep_bwd<Real, NE, T, R, EV>;
     cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -190,9 +190,10 @@ int fgt1d_geometry_apply(fgt1d_plan plan, int64_t M, int64_t N, const double* al
 /* Sweep tile shape and its autotuner.  Every sweep tile holds 4096 merged points (the
  * chunk of the associative scan, Sec. 4 recurrences split per tile); a tile runs as
  * `threads` threads of 4096 / threads consecutive points each.  threads = 128 (32
- * points per thread) or 256 (16 points per thread); 0 selects the default of the plan's
- * precision (FP64: 128, FP32 and F32X2: 256).  Results differ between shapes only by
- * rounding.  fgt1d_plan_get_tile returns the shape in use (never 0).  Not thread-safe
+ * points per thread) or 256 (16 points per thread); 0 selects the default, 256 (the
+ * gradient sweeps of fgt1d_backward then use 128 for plans with n_e > 5).  Results
+ * differ between shapes only by rounding.  fgt1d_plan_get_tile returns the shape of the
+ * transform sweeps (never 0).  Not thread-safe
  * with a concurrent execute on the same plan.  Errors: FGT1D_EINVAL. */
 int fgt1d_plan_set_tile(fgt1d_plan plan, int threads);
 int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads);

@@ -204,13 +204,17 @@ SweepConsts make_consts(const fgt1d_plan_s& p) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGT1D_OK : FGT1D_ECUDA; }
 
-// Sweep tile shape index (0: 128 threads x 32 points, 1: 256 x 16): the plan's explicit
-// choice, else 256 x 16 for the FP32-pipe kernels and 128 x 32 for the FP64 ones.
-int tile_threads_of(const fgt1d_plan_s& p, bool fp32_pipe) {
-    if (p.tile_threads) return p.tile_threads;
-    return fp32_pipe ? 256 : 128;
+// Sweep tile shape (threads per 4096-point tile): the plan's explicit choice, else
+// 256 x 16 (measured faster on every value-channel workload).
+int tile_threads_of(const fgt1d_plan_s& p) { return p.tile_threads ? p.tile_threads : 256; }
+// Shape index (0: 128 x 32, 1: 256 x 16) for sweeps with evaluation channels ev.  By
+// default the gradient sweeps (ev != 1) of plans with more than five terms run 128 x 32:
+// they keep all terms in one group, and at 256 x 16 their scan region would leave one
+// tile per SM.
+int shape_index(const fgt1d_plan_s& p, int ev = 1) {
+    if (!p.tile_threads && ev != 1 && p.n_e > 5) return 0;
+    return tile_threads_of(p) == 256 ? 1 : 0;
 }
-int shape_index(const fgt1d_plan_s& p, bool fp32_pipe) { return tile_threads_of(p, fp32_pipe) == 256 ? 1 : 0; }
 
 // Where the items come from: one item (M targets, N sources, the plan's delta), or B
 // items from device offsets and optional per-item bandwidths.
@@ -274,9 +278,9 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
-    if (f32) e = launch_sweeps_f32(w, c, st, mid, ev, shape_index(p, true));
-    else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid, shape_index(p, true));
-    else e = launch_sweeps_f64(w, c, st, mid, ev, shape_index(p, false));
+    if (f32) e = launch_sweeps_f32(w, c, st, mid, ev, shape_index(p, ev));
+    else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid, shape_index(p, ev));
+    else e = launch_sweeps_f64(w, c, st, mid, ev, shape_index(p, ev));
     if (e == cudaSuccess) e = rec(3);
     if (e == cudaSuccess && coinc) {
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
@@ -549,7 +553,7 @@ uint64_t geometry_tag(const fgt1d_plan_s& p, int64_t M, int64_t N) {
     mix(&p.delta, 8);
     mix(p.tau_re, sizeof(double) * (size_t)p.n_e);
     mix(p.tau_im, sizeof(double) * (size_t)p.n_e);
-    const int shape = shape_index(p, false);  // the table layout follows the tile shape
+    const int shape = shape_index(p);  // the table layout follows the tile shape
     mix(&shape, sizeof(shape));
     return h;
 }
@@ -590,7 +594,7 @@ extern "C" int fgt1d_geometry_bind(fgt1d_plan plan, const double* x, int64_t M, 
     if (e == cudaSuccess) e = launch_sort(sa, st);
     SweepArgs w = sweep_args(nullptr, N, nullptr, nullptr, ws, L);
     SweepConsts c = make_consts(*plan);
-    if (e == cudaSuccess) e = launch_fill_table(w, c, shape_index(*plan, false), st);
+    if (e == cudaSuccess) e = launch_fill_table(w, c, shape_index(*plan), st);
     if (e == cudaSuccess)
         e = launch_geometry_tag(reinterpret_cast<uint64_t*>(ws + L.header + kTagOffset), geometry_tag(*plan, M, N), st);
     return cuda_status(e);
@@ -620,7 +624,7 @@ extern "C" int fgt1d_geometry_apply(fgt1d_plan plan, int64_t M, int64_t N, const
     SweepArgs w = sweep_args(alpha, N, u, nullptr, ws, L);
     w.reuse = 1;
     SweepConsts c = make_consts(p);
-    if (e == cudaSuccess) e = launch_sweeps_f64(w, c, st, nullptr, 1, shape_index(p, false));
+    if (e == cudaSuccess) e = launch_sweeps_f64(w, c, st, nullptr, 1, shape_index(p));
     if (e == cudaSuccess && (p.flags & FGT1D_EXACT_SELF)) {
         double* A = reinterpret_cast<double*>(ws + L.coinc);
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
@@ -643,7 +647,7 @@ extern "C" int fgt1d_plan_set_tile(fgt1d_plan plan, int threads) {
 
 extern "C" int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads) {
     if (!plan || !threads) return FGT1D_EINVAL;
-    *threads = tile_threads_of(*plan, (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) != 0);
+    *threads = tile_threads_of(*plan);
     return FGT1D_OK;
 }
 
@@ -658,7 +662,7 @@ extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, cons
     const int prev = plan->tile_threads;
     auto done = [&](int t) {
         plan->tile_threads = t;
-        if (threads_out) *threads_out = tile_threads_of(*plan, (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) != 0);
+        if (threads_out) *threads_out = tile_threads_of(*plan);
         return FGT1D_OK;
     };
     if (const char* env = std::getenv("FGT1D_TILE_THREADS")) {

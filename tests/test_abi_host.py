@@ -94,7 +94,7 @@ def test_plan_errors(L):
 def test_tile_shape_setting(L):
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import _lib
-    assert fgt.Plan(1.0, 1e-6).tile_threads == 128
+    assert fgt.Plan(1.0, 1e-6).tile_threads == 256
     assert fgt.Plan(1.0, 1e-6, precision="fp32").tile_threads == 256
     p = fgt.Plan(1.0, 1e-10, precision="f32x2")
     assert p.tile_threads == 256

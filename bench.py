@@ -269,6 +269,23 @@ def main():
     if traffic is not None:
         roofline["traffic"] = traffic * P
 
+    # end to end through the host-buffer entry point (copies inside the timed region),
+    # right after the headline so that both see the same GPU state
+    hx = torch.from_numpy(x).pin_memory().numpy()
+    hy = torch.from_numpy(y).pin_memory().numpy()
+    ha = torch.from_numpy(a).pin_memory().numpy()
+    hu = torch.empty(M, dtype=torch.float64).pin_memory().numpy()
+    hws = fgt.Workspace(dev)
+    fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
+    barrier()
+    e2e_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    del hws
+
     also = []
     if not args.no_also:
         for cfg in ALSO:
@@ -288,22 +305,6 @@ def main():
         extra["precision_split"] = precision_split(args, dev, world, P)
         extra["differentiation"] = differentiation(dev, world)
         extra["batched"] = batched(dev, world)
-
-    # end to end through the host-buffer entry point (copies inside the timed region)
-    hx = torch.from_numpy(x).pin_memory().numpy()
-    hy = torch.from_numpy(y).pin_memory().numpy()
-    ha = torch.from_numpy(a).pin_memory().numpy()
-    hu = torch.empty(M, dtype=torch.float64).pin_memory().numpy()
-    hws = fgt.Workspace(dev)
-    fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
-    barrier()
-    e2e_steps = max(2, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        fgt.execute_host(plan, hx, hy, ha, out=hu, workspace=hws)
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    del hws
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -257,7 +257,8 @@ SweepArgs sweep_args(const double* alpha, int64_t N, double* u, double* out2, ch
 // receives the per-target sums of coincident source strengths.
 int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
                  const ItemSource& src, double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L,
-                 cudaStream_t st, cudaEvent_t const* evs = nullptr, bool self = false) {
+                 cudaStream_t st, cudaEvent_t const* evs = nullptr, bool self = false,
+                 cudaEvent_t alpha_ready = nullptr) {
     auto rec = [&](int i) { return (evs && evs[i]) ? cudaEventRecord(evs[i], st) : cudaSuccess; };
     cudaError_t e = rec(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
@@ -272,6 +273,8 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     SortArgs sa = sort_args(x, y, N, ws, L);
     e = launch_sort(sa, st);
     if (e == cudaSuccess) e = rec(1);
+    // strengths copied on another stream meanwhile (the sort does not read them)
+    if (e == cudaSuccess && alpha_ready) e = cudaStreamWaitEvent(st, alpha_ready, 0);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
     w.self = self ? 1 : 0;
@@ -292,14 +295,16 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
 }
 
 int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
-                  double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr) {
+                  double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr,
+                  cudaEvent_t alpha_ready = nullptr) {
     if (M == 0) return FGT1D_OK;
     if (N == 0) return cuda_status(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)M, st));
     if (!(p.flags & FGT1D_EXACT_SELF))
-        return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, evs);
+        return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, evs, false,
+                            alpha_ready);
     // coincident pairs: add (1 - S_n(0)) times the coincident source strengths
     double* A = reinterpret_cast<double*>(ws + L.coinc);
-    int r = run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, A, ws, L, st, evs);
+    int r = run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, A, ws, L, st, evs, false, alpha_ready);
     if (r) return r;
     double s0 = 0.0;
     for (int k = 0; k < p.n_e; ++k) s0 += p.w_re[k];
@@ -478,12 +483,33 @@ extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t
     double* dy = reinterpret_cast<double*>(ws + L.hy);
     double* da = reinterpret_cast<double*>(ws + L.ha);
     double* du = reinterpret_cast<double*>(ws + L.hu);
-    if (cudaMemcpyAsync(dx, x_host, sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dy, y_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(da, alpha_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    // coordinates on the caller's stream; the strengths on a second stream, overlapping
+    // the sort, which does not read them
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_alpha = nullptr;
+    auto release = [&]() {
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_alpha) cudaEventDestroy(ev_alpha);
+        if (s2) cudaStreamDestroy(s2);
+    };
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_alpha, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev_in, st) != cudaSuccess || cudaStreamWaitEvent(s2, ev_in, 0) != cudaSuccess ||
+        cudaMemcpyAsync(da, alpha_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, s2) != cudaSuccess ||
+        cudaEventRecord(ev_alpha, s2) != cudaSuccess ||
+        cudaMemcpyAsync(dx, x_host, sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dy, y_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        release();
         return FGT1D_ECUDA;
-    r = run_transform(*plan, dx, M, dy, da, N, du, ws, L, st);
-    if (r) return r;
+    }
+    r = run_transform(*plan, dx, M, dy, da, N, du, ws, L, st, nullptr, ev_alpha);
+    if (r) {
+        cudaStreamSynchronize(s2);
+        release();
+        return r;
+    }
+    release();  // the stream and events go once their work is done
     if (cudaMemcpyAsync(u_host, du, sizeof(double) * (size_t)M, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return FGT1D_ECUDA;
     return fgt1d_check(workspace, ws_bytes, stream);

@@ -24,20 +24,25 @@
 //            predecessor, using the published span multipliers), publish the
 //            inclusive value;
 //   phase C  per term: apply the carries, final pass, evaluation at targets.
-// Per-point multipliers use a Taylor polynomial of warp-uniform degree chosen from
-// the warp's largest gap (integer compares on the bit pattern of theta), falling back
-// to exp/sincos for large gaps.
+// When the scan region of all terms would not fit the occupancy target, the terms run
+// in equal groups, each with its own phases A-C (SweepGroup).  Per-point multipliers
+// use a Taylor polynomial of warp-uniform degree chosen from the warp's largest gap
+// (integer compares on the bit pattern of theta), falling back to exp/sincos for large
+// gaps.
 //
-// FP64 path (Real = double): every step in FP64.  The forward kernel stores the
-// multipliers (16 B per point and term): on GB300 one DFMA costs as much issue time
-// as 62 FFMAs, and reloading 16 B is cheaper than the 6-10 DFMAs of a multiplier.
-// Inside each 4096-point tile the table is thread-interleaved: the
+// FP64 path (Real = double): FP64 accuracy at every step.  The forward kernel stores
+// the multipliers (16 B per point and term): on GB300 one DFMA costs as much issue time
+// as 62 FFMAs, and reloading 16 B is cheaper than the 5-10 DFMAs of a multiplier.  For
+// small |tau theta| the multiplier's cubic-and-up Taylor tail runs on the FP32 pipe
+// (taylor_hybrid).  Inside each 4096-point tile the table is thread-interleaved: the
 // multiplier of a tile's point t R + r sits at slot r T + t, so that the R loads or
 // stores of a warp's 32 threads are each one contiguous 512-byte segment.
 // FP32 path (Real = float): gaps, multipliers and in-tile recurrences in FP32
 // complex; tile aggregates, span multipliers and carries in FP64.  Gaps come from the
 // integer difference of the sorted keys and FP64<->FP32 conversions are done with
 // integer bit operations, so the per-point work issues no FP64-pipe instruction.
+// Double-float path (Real = dfloat): the FP32 path's structure with pairs of floats
+// (about 48 significant bits) for gaps, multipliers and recurrences.
 #pragma once
 
 #include <cuda_runtime.h>

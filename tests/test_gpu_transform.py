@@ -210,6 +210,25 @@ def test_tile_shapes_vs_recurrence(cuda, prec, tile):
     assert rel_inf(u, ref, a) <= {"fp64": TOL_ARITH64, "f32x2": TOL_ARITH_DF, "fp32": 5e-6}[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f32x2"])
+@pytest.mark.parametrize("nodes", ["cf14", "hyperbolic16"])
+def test_term_groups_vs_recurrence(cuda, prec, nodes):
+    """Plans of n_e = 7 and 8 terms: at 256 x 16 the value sweeps split the terms into
+    groups (two phases A-C per tile); both shapes against the oracle recurrence."""
+    if nodes == "cf14":
+        n, tau, W, En = soe_cf.plan_soe(1e-10)
+    else:
+        tau, W, En = soe_cf.hyperbolic_soe(16)
+    x, y, a = inputs.mixture(30000, 25000, seed=17)
+    delta = 1e-4
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    tol = {"fp64": TOL_ARITH64, "f32x2": TOL_ARITH_DF, "fp32": 5e-6}[prec]
+    for tile in (256, 128):
+        plan = fgt.Plan(delta, soe=(tau, W), precision=prec)
+        plan.tile_threads = tile
+        assert rel_inf(gpu_transform(plan, x, y, a), ref, a) <= tol, tile
+
+
 def test_autotune_picks_the_faster_shape(cuda):
     x, y, a = inputs.uniform(300000, 300000, seed=3)
     X, Y, A = (torch.from_numpy(v).to(cuda) for v in (x, y, a))

@@ -439,10 +439,12 @@ __device__ __forceinline__ void with_degree(int deg, Body&& body) {
     }
 }
 
-// Single multiplier with a runtime degree (thread and tile spans).
+// Single multiplier for a warp whose largest theta has bit pattern hw (thread spans):
+// the degree, and the FP64 head + FP32 tail form when it applies, follow from hw.
 template <typename Real>
-__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, int deg, Real th, Real& mr, Real& mi) {
-    with_degree<Real>(deg, [&](auto Dc) { taylor<Real>(c, k, Dc, th, mr, mi); });
+__device__ __forceinline__ void multiplier(const SweepConsts& c, int k, uint32_t hw, Real th, Real& mr, Real& mi) {
+    const bool hyb = std::is_same<Real, double>::value && hw <= c.theta_hyb_lim[k];
+    with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) { taylor<Real>(c, k, Dc, th, mr, mi, hyb); });
 }
 
 __device__ __forceinline__ void publish_agg(TileDesc* d, double ar, double ai, double Mr, double Mi) {
@@ -625,10 +627,27 @@ __device__ __forceinline__ dfloat gap_df(double a, double b) {
     return to_real<dfloat>(b - a);
 }
 
+// b - a (b >= a) in FP64 without an FP64 subtraction: for normal a and b of one sign in
+// one binade the integer difference of the bit patterns is the exact difference in
+// units of the binade's ulp (below 2^52, so exactly representable); otherwise FP64.
+__device__ __forceinline__ double gap_f64(double a, double b) {
+    const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+    const uint32_t ea = (uint32_t)(ba >> 52) & 0x7FFu, eb = (uint32_t)(bb >> 52) & 0x7FFu;
+    if (ea == eb && ea > 53 && ea != 0x7FF && ((ba ^ bb) >> 63) == 0) {
+        const uint64_t d = bb >= ba ? bb - ba : ba - bb;
+        if (d == 0) return 0.0;
+        const int msb = 63 - __clzll((long long)d);  // < 52
+        // d * 2^(ea - 1075): exponent field ea - 52 + msb (>= 1 since ea > 53)
+        const uint64_t bits = ((uint64_t)(ea - 52 + msb) << 52) | ((d << (52 - msb)) & 0xFFFFFFFFFFFFFull);
+        return __longlong_as_double((long long)bits);
+    }
+    return b - a;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real gap_real(double a, double b, const Scale& sc);
 template <>
-__device__ __forceinline__ double gap_real<double>(double a, double b, const Scale& sc) { return sc.d * (b - a); }
+__device__ __forceinline__ double gap_real<double>(double a, double b, const Scale& sc) { return sc.d * gap_f64(a, b); }
 template <>
 __device__ __forceinline__ float gap_real<float>(double a, double b, const Scale& sc) { return sc.f * gap_f32(a, b); }
 template <>
@@ -671,15 +690,32 @@ __device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc,
                                              int dir, bool first_in_dir, double Mr, double Mi, double (*s_w)[NW][4],
                                              double (*s_win)[NW][2], int k) {
     const int lane = threadIdx.x & 31;
+    // lane q < NW takes the warp at sweep position q and the lanes scan the pairs
+    // (M, F) -> h = M h + F over positions (log2 NW shuffle steps); lanes >= NW hold the
+    // identity
+    const int ww = dir < 0 ? lane : NW - 1 - lane;
     double Pr = 1, Pi = 0, Qr = 0, Qi = 0;
-    double pre0 = 1, pre1 = 0, pre2 = 0, pre3 = 0;  // prefix before warp `lane` (lanes < NW)
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        const int ww = dir < 0 ? q : NW - 1 - q;
-        if (ww == lane) { pre0 = Pr; pre1 = Pi; pre2 = Qr; pre3 = Qi; }
-        cfma<double>(s_w[k][ww][0], s_w[k][ww][1], Qr, Qi, s_w[k][ww][2], s_w[k][ww][3], Qr, Qi);
-        cmul<double>(s_w[k][ww][0], s_w[k][ww][1], Pr, Pi, Pr, Pi);
+    if (lane < NW) {
+        Pr = s_w[k][ww][0];
+        Pi = s_w[k][ww][1];
+        Qr = s_w[k][ww][2];
+        Qi = s_w[k][ww][3];
     }
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+        const double por = __shfl_up_sync(0xffffffffu, Pr, o), poi = __shfl_up_sync(0xffffffffu, Pi, o);
+        const double qor = __shfl_up_sync(0xffffffffu, Qr, o), qoi = __shfl_up_sync(0xffffffffu, Qi, o);
+        if (lane >= o) {
+            cfma<double>(Pr, Pi, qor, qoi, Qr, Qi, Qr, Qi);
+            cmul<double>(Pr, Pi, por, poi, Pr, Pi);
+        }
+    }
+    // exclusive prefix (the state map before this lane's warp) and the tile aggregate
+    double pre0 = __shfl_up_sync(0xffffffffu, Pr, 1), pre1 = __shfl_up_sync(0xffffffffu, Pi, 1);
+    double pre2 = __shfl_up_sync(0xffffffffu, Qr, 1), pre3 = __shfl_up_sync(0xffffffffu, Qi, 1);
+    if (lane == 0) { pre0 = 1; pre1 = 0; pre2 = 0; pre3 = 0; }
+    Qr = __shfl_sync(0xffffffffu, Qr, NW - 1);
+    Qi = __shfl_sync(0xffffffffu, Qi, NW - 1);
     TileDesc* dd = desc + tile * NE + k;
     double Cr = 0, Ci = 0;
     if (lane == 0) publish_agg(dd, Qr, Qi, Mr, Mi);
@@ -697,8 +733,8 @@ __device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc,
     if (lane < NW) {
         double xr, xi;
         cfma<double>(pre0, pre1, Cr, Ci, pre2, pre3, xr, xi);
-        s_win[k][lane][0] = xr;
-        s_win[k][lane][1] = xi;
+        s_win[k][ww][0] = xr;
+        s_win[k][ww][1] = xi;
     }
 }
 
@@ -883,7 +919,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                         }
                     });
                 }
-                multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+                multiplier<Real>(c, k, hsp, thsp, Mr, Mi);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1125,7 +1161,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
                 }
             });
             Real Mr, Mi;
-            multiplier<Real>(c, k, taylor_degree<Real>(c, k, hsp), thsp, Mr, Mi);
+            multiplier<Real>(c, k, hsp, thsp, Mr, Mi);
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);

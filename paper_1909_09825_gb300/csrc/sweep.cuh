@@ -339,25 +339,80 @@ __device__ __forceinline__ void taylor_split<dfloat>(const SweepConsts& c, int k
     }
 }
 
-// FP64 exp(-tau_k theta) of degree D >= 3 for |tau_k| theta <= 2^-10 (warp-uniform): the
-// head 1 + c_1 theta + c_2 theta^2 in FP64 (Horner, 4 DFMA + 1 DADD), the tail
-// theta^3 sum_{j>=3} c_j theta^(j-3) in FP32 (Horner on the FP32 pipe, converted exactly).
-// The tail is below |tau theta|^3 / 6 <= 2^-32.6 and its FP32 rounding below (D + 2)
-// 2^-24 of it, so the result keeps the FP64 truncation rule's 2^-53 accuracy while the
-// FP64 pipe, the bound of these kernels, does 5 operations instead of 2 D.
+// Signed fixed point with 2^-62 resolution, for sums of a few floats below 2 in size.
+// f32_to_fix62 truncates toward zero below 2^-62; fix62_to_f64 rounds to nearest.
+__device__ __forceinline__ int64_t f32_to_fix62(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e == 0) return 0;  // zero, or below 2^-126
+    const int64_t m = (int64_t)((b & 0x7FFFFFu) | 0x800000u);  // f = m 2^(e - 150)
+    const int sh = e - 88;                                       // f 2^62 = m 2^sh
+    const int64_t v = sh >= 0 ? (m << sh) : (sh > -25 ? (m >> -sh) : 0);
+    return (b >> 31) ? -v : v;
+}
+__device__ __forceinline__ double fix62_to_f64(int64_t v) {
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const uint64_t a = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+    const int msb = 63 - __clzll((long long)a);
+    int e = msb - 62;
+    uint64_t mant;
+    if (msb > 52) {
+        const int sh = msb - 52;
+        mant = (a >> sh) + ((a >> (sh - 1)) & 1ull);
+        if (mant >> 53) {
+            mant >>= 1;
+            ++e;
+        }
+    } else {
+        mant = a << (52 - msb);
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// FP64 exp(-tau_k theta) of degree D >= 2 for |tau_k| theta <= 2^-10 (warp-uniform), with
+// two FP64 operations: m = (1 + T) + c_1 theta and i(T') + c_1 theta by one DFMA each, where
+// T = sum_{j>=2} c_j theta^j is formed off the FP64 pipe.  theta is split exactly into
+// two floats (top 24 bits, rest), c_2 theta^2 is a float pair (FMA two-products with
+// c_2 as a float pair), the terms of degree >= 3 are one FP32 Horner sum (below
+// |tau theta|^3 / 6 <= 2^-32.6, so its FP32 rounding is below 2^-54), and 1 + T is
+// summed in 62-bit fixed point and rounded once to FP64.  The result carries the
+// rounding of two FP64 operations, like the full FP64 polynomial's last steps.
 template <int D>
 __device__ __forceinline__ void taylor_hybrid(const SweepConsts& c, int k, double th, double& mr, double& mi) {
-    const float t = f64_to_f32(th);
-    float ar = c.tcf_re[k][D], ai = c.tcf_im[k][D];
-#pragma unroll
-    for (int j = D - 1; j >= 3; --j) {
-        ar = __fmaf_rn(ar, t, c.tcf_re[k][j]);
-        ai = __fmaf_rn(ai, t, c.tcf_im[k][j]);
+    const uint64_t tb = (uint64_t)__double_as_longlong(th);
+    const int E = (int)(tb >> 52);  // theta >= 0
+    float thf = 0.f, tlf = 0.f;
+    if (E > 1023 - 100) {  // below 2^-100 the theta^2 terms vanish far under 2^-53
+        const uint64_t m = tb & 0xFFFFFFFFFFFFFull;
+        thf = __uint_as_float(((uint32_t)(E - 896) << 23) | (uint32_t)(m >> 29));
+        tlf = u64_scaled_to_f32(m & 0x1FFFFFFFull, E - 1075);
     }
-    const float t3 = __fmul_rn(__fmul_rn(t, t), t);
-    const double tr = f32_to_f64(__fmul_rn(ar, t3)), ti = f32_to_f64(__fmul_rn(ai, t3));
-    mr = fma(fma(c.tc_re[k][2], th, c.tc_re[k][1]), th, 1.0) + tr;
-    mi = fma(fma(c.tc_im[k][2], th, c.tc_im[k][1]), th, ti);
+    // theta^2 = p + pe
+    const float p = __fmul_rn(thf, thf);
+    float pe = __fmaf_rn(thf, thf, -p);
+    pe = __fmaf_rn(__fmul_rn(2.f, thf), tlf, pe);
+    // c_2 theta^2 = q + qe (real and imaginary parts)
+    const float c2r = c.tcd_re_hi[k][2], c2rl = c.tcd_re_lo[k][2], c2i = c.tcd_im_hi[k][2], c2il = c.tcd_im_lo[k][2];
+    const float qr = __fmul_rn(c2r, p), qi = __fmul_rn(c2i, p);
+    float qer = __fmaf_rn(c2r, p, -qr), qei = __fmaf_rn(c2i, p, -qi);
+    qer = __fmaf_rn(c2r, pe, __fmaf_rn(c2rl, p, qer));
+    qei = __fmaf_rn(c2i, pe, __fmaf_rn(c2il, p, qei));
+    if constexpr (D >= 3) {
+        float ar = c.tcf_re[k][D], ai = c.tcf_im[k][D];
+#pragma unroll
+        for (int j = D - 1; j >= 3; --j) {
+            ar = __fmaf_rn(ar, thf, c.tcf_re[k][j]);
+            ai = __fmaf_rn(ai, thf, c.tcf_im[k][j]);
+        }
+        const float t3 = __fmul_rn(p, thf);
+        qer = __fmaf_rn(ar, t3, qer);
+        qei = __fmaf_rn(ai, t3, qei);
+    }
+    const double sr = fix62_to_f64((int64_t(1) << 62) + f32_to_fix62(qr) + f32_to_fix62(qer));
+    const double si = fix62_to_f64(f32_to_fix62(qi) + f32_to_fix62(qei));
+    mr = fma(c.tc_re[k][1], th, sr);
+    mi = fma(c.tc_im[k][1], th, si);
 }
 
 // A Taylor degree known only at run time (warp-uniform): the double-float path, whose
@@ -375,7 +430,7 @@ struct RtDeg {
 template <typename Real, typename Dc>
 __device__ __forceinline__ void taylor(const SweepConsts& c, int k, Dc dc, Real th, Real& mr, Real& mi,
                                        bool hybrid = false) {
-    if constexpr (Dc::value >= 3 && std::is_same<Real, double>::value) {
+    if constexpr (Dc::value >= 2 && std::is_same<Real, double>::value) {
         if (hybrid) {
             taylor_hybrid<Dc::value>(c, k, th, mr, mi);
             return;

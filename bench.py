@@ -418,12 +418,24 @@ def identical_points(X, A, dev, world, stream):
         fgt.transform_self(plan, X, A_, out=U, workspace=ws)  # checks the device status
         ms_gen = _event_time(lambda: fgt.transform(plan, X, X, A_, out=U, workspace=ws, sync_check=False), 3, 2,
                              stream)
-        out.append({"eps": eps, "n_e": plan.n_e, "points_per_s": world * N / (ms_self * 1e-3), "ms": ms_self,
-                     "general_path_on_x_x_ms": ms_gen, "speedup": ms_gen / ms_self})
+        out.append({"points": "uniform", "eps": eps, "n_e": plan.n_e, "points_per_s": world * N / (ms_self * 1e-3),
+                     "ms": ms_self, "general_path_on_x_x_ms": ms_gen, "speedup": ms_gen / ms_self})
         del ws
         torch.cuda.empty_cache()
-    return {"workload": "N=2^%d uniform points as targets and sources, alpha ~ N(0,1), delta=1 "
-                        "(Table 5.1's shape), FP64" % int(np.log2(N)), "unit": "N points/s", "runs": out}
+    # Sec. 5's second point set: Chebyshev points on [0, 1]
+    from paper_1909_09825_gb300 import inputs
+    xc, _ = inputs.chebyshev(N, seed=0)
+    XC = torch.from_numpy(xc).to(dev)
+    plan = fgt.Plan(1.0, 1e-6)
+    ws = fgt.Workspace(dev)
+    ms_c = _event_time(lambda: fgt.transform_self(plan, XC, A_, out=U, workspace=ws, sync_check=False), 3, 3, stream)
+    fgt.transform_self(plan, XC, A_, out=U, workspace=ws)
+    out.append({"points": "chebyshev", "eps": 1e-6, "n_e": plan.n_e, "points_per_s": world * N / (ms_c * 1e-3),
+                "ms": ms_c})
+    del ws, XC
+    torch.cuda.empty_cache()
+    return {"workload": "N=2^%d uniform (Table 5.1's shape) or Chebyshev points on [0,1] as targets and sources, "
+                        "alpha ~ N(0,1), delta=1, FP64" % int(np.log2(N)), "unit": "N points/s", "runs": out}
 
 
 def precision_split(args, dev, world, P_unused):

@@ -82,6 +82,15 @@ def with_ties(M, N, seed=0, n_distinct=64):
     return x, y, a
 
 
+def chebyshev(N, seed=0, alpha="normal"):
+    """The paper's second point set (Sec. 5): N Chebyshev points mapped to [0, 1],
+    x_i = (1 + cos(pi (2 i + 1) / (2 N))) / 2 (in decreasing order, clustered at both
+    ends), with seeded strengths alpha ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    x = 0.5 * (1.0 + np.cos(np.pi * (2.0 * np.arange(N) + 1.0) / (2.0 * N)))
+    return x, _alpha(rng, N, alpha)
+
+
 def batched_device(B, device, seed=0, lo=1e2, hi=1e6, dlo=1e-6, dhi=1e-1):
     """Batched workload drawn on the device (torch generator) for large B: item sizes
     M_b = N_b and bandwidths from batched_sizes (numpy, seed), then x, y ~ U[0,1) and

@@ -50,6 +50,19 @@ def test_self_equals_merged_transform(cuda):
     assert rel_inf(u, gpu_transform(plan, x, x, a), a) <= TOL_ARITH64
 
 
+@pytest.mark.parametrize("delta", [1.0, 1e-6])
+def test_self_chebyshev_points(cuda, delta):
+    """Sec. 5's Chebyshev points (gaps from 1.2e-8 at the ends to 7.9e-5 in the middle)."""
+    x, a = inputs.chebyshev(20000, seed=3)
+    n, tau, W, En = soe_cf.plan_soe(1e-10)
+    plan = fgt.Plan(delta, soe=(tau, W))
+    u = _self(plan, x, a, cuda)
+    assert rel_inf(u, oracle.recurrence_self(x, a, delta, tau, W), a) <= TOL_ARITH64
+    plan2 = fgt.Plan(delta, 1e-10)
+    idx = np.arange(0, 20000, 499)
+    assert rel_inf(_self(plan2, x, a, cuda)[idx], oracle.direct(x[idx], x, a, delta), a) <= 2e-10 + 1e-13
+
+
 def test_self_large_vs_direct(cuda):
     """Table 5.1's workload shape (uniform points, delta = 1) at N = 2^22, sampled
     targets against the direct Gauss sum."""

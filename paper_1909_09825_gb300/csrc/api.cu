@@ -54,9 +54,8 @@ Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sw
     L.valsA = off; off += align_up(sizeof(uint32_t) * Pp);
     L.valsB = off; off += align_up(sizeof(uint32_t) * Pp);
     if (sweeps) {
-        // the multiplier table serves the FP64 sweeps (transform, and gradients of F32X2 plans)
-        const bool f64_sweeps = !(flags & FGT1D_FP32) && (!(flags & FGT1D_F32X2) || grad);
-        if (f64_sweeps) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
+        // the multiplier table serves the FP64 and double-float sweeps (16 B per point and term)
+        if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
         L.fwd = off; off += align_up(sizeof(double) * Pp);
         if (flags & FGT1D_EXACT_SELF) { L.coinc = off; off += align_up(sizeof(double) * (size_t)M); }
     }

@@ -632,6 +632,31 @@ struct SweepMinBlocks { static constexpr int value = sizeof(Real) == 8 ? 2 : 3; 
 template <int R>
 __device__ __forceinline__ int pad(int i) { return i + i / R; }
 
+// Multiplier table entries (16 bytes): an FP64 complex, or a double-float complex stored
+// as (re.hi, re.lo, im.hi, im.lo).
+template <typename Real>
+struct TableEntry;
+template <>
+struct TableEntry<double> {
+    __device__ static __forceinline__ void store(double2* p, double mr, double mi) { *p = make_double2(mr, mi); }
+    __device__ static __forceinline__ void load(const double2* p, double& mr, double& mi) {
+        const double2 m = *p;
+        mr = m.x;
+        mi = m.y;
+    }
+};
+template <>
+struct TableEntry<dfloat> {
+    __device__ static __forceinline__ void store(double2* p, dfloat mr, dfloat mi) {
+        *reinterpret_cast<float4*>(p) = make_float4(mr.hi, mr.lo, mi.hi, mi.lo);
+    }
+    __device__ static __forceinline__ void load(const double2* p, dfloat& mr, dfloat& mi) {
+        const float4 m = *reinterpret_cast<const float4*>(p);
+        mr = dfloat(m.x, m.y);
+        mi = dfloat(m.z, m.w);
+    }
+};
+
 
 template <typename Real>
 __device__ __forceinline__ Real to_real(double v);
@@ -828,7 +853,9 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     using SM = SweepSmem<Real, NG, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
-    constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    constexpr bool kF64 = std::is_same<Real, double>::value;
+    // multipliers stored by phase A and reloaded (FP64 and double-float); FP32 recomputes
+    constexpr bool kTab = kF64 || std::is_same<Real, dfloat>::value;
     constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     static_assert((EV & 2) == 0 || NG == NE, "the derivative channel runs its terms as one group");
@@ -947,7 +974,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 Mi = 0;
             } else {
                 // this thread's R multipliers are slots r T + tid of the tile (interleaved table)
-                double2* __restrict__ mt = kF64 ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
+                double2* __restrict__ mt = kTab ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
                 bool loaded = false;
                 if constexpr (kF64) {
                     if (reuse) {
@@ -967,8 +994,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                         for (int r = 0; r < R; ++r) {
                             Real mr, mi;
                             taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi, hyb);
-                            if constexpr (kF64) {
-                                if (i0 + r < nvalid) mt[r * T] = make_double2((double)mr, (double)mi);
+                            if constexpr (kTab) {
+                                if (i0 + r < nvalid) TableEntry<Real>::store(mt + r * T, mr, mi);
                             }
                             cfma_ra<Real>(mr, mi, fr, fi, strength(r), fr, fi);
                         }
@@ -1040,6 +1067,20 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                     cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
                     eval(r);
                 }
+            } else if constexpr (kTab) {
+                // double-float: multipliers from the table; the value channel accumulates in
+                // the targets' own (zero) strength slots
+                const double2* __restrict__ mt = a.mult + (int64_t)k * a.Ppad + base + tid;
+#pragma unroll kUnrollC
+                for (int r = 0; r < R; ++r) {
+                    Real mr = Real(1), mi = Real(0);
+                    if (i0 + r < nvalid) TableEntry<Real>::load(mt + r * T, mr, mi);
+                    const bool tg = (tmask >> r) & 1u;
+                    Real* slot = &s_al[pad<R>(i0 + r)];
+                    const Real v = *slot;
+                    cfma_ra<Real>(mr, mi, fr, fi, tg ? Real(0) : v, fr, fi);
+                    if (tg) *slot = fma(Wr, fr, fma(-Wi, fi, v));
+                }
             } else {
                 // recomputed multipliers: the value channel accumulates in the targets' own
                 // (zero) strength slots, so the loop needs no register array and is only
@@ -1087,7 +1128,9 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     using SM = SweepSmem<Real, NG, T, R>;
     constexpr int TILE = T * R;
     constexpr int NW = T / 32;
-    constexpr bool kF64 = std::is_same<Real, double>::value;  // stored multiplier table
+    constexpr bool kF64 = std::is_same<Real, double>::value;
+    // multipliers reloaded from the forward sweep's table (FP64 and double-float)
+    constexpr bool kTab = kF64 || std::is_same<Real, dfloat>::value;
     constexpr int kUnrollC = sizeof(Real) == 8 ? 4 : 8;       // phase C unroll, recomputed multipliers
     static_assert(!((EV & 2) && std::is_same<Real, dfloat>::value), "no derivative channel in double-float");
     static_assert((EV & 2) == 0 || NG == NE, "the derivative channel runs its terms as one group");
@@ -1133,7 +1176,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     const double znext = s_z[pad<R>(TILE)], zfirst = s_z[0];
     uint32_t hw = 0;
     Real thr[R];
-    if constexpr (!kF64) {
+    if constexpr (!kTab) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = i0 + r;
@@ -1153,7 +1196,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     }
     const uint32_t hsp = __reduce_max_sync(0xffffffffu, theta_hw<Real>(thsp));
     __syncthreads();
-    if constexpr (!kF64) {
+    if constexpr (!kTab) {
 #pragma unroll
         for (int r = 0; r < R; ++r) s_th[pad<R>(i0 + r)] = thr[r];
     }
@@ -1175,12 +1218,12 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     // slot (+1), which for the last thread is the next tile's slot 0
     const int64_t next_off = tid + 1 < T ? 1 : (int64_t)TILE - tid;
     auto mult_at = [&](int k, auto Dc, int r, Real& mr, Real& mi) {
-        if constexpr (kF64) {
+        if constexpr (kTab) {
             const double2* mt = a.mult + (int64_t)k * a.Ppad + base + tid;
-            const double2 m = local + i0 + r + 1 < preal ? mt[r + 1 < R ? (int64_t)(r + 1) * T : next_off]
-                                                         : make_double2(0.0, 0.0);
-            mr = m.x;
-            mi = m.y;
+            mr = Real(0);
+            mi = Real(0);
+            if (local + i0 + r + 1 < preal)
+                TableEntry<Real>::load(mt + (r + 1 < R ? (int64_t)(r + 1) * T : next_off), mr, mi);
         } else {
             taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
         }
@@ -1204,7 +1247,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
         if (g0 > 0) __syncthreads();  // the previous group's phase C has read s_scan
 #pragma unroll 1
         for (int k = g0; k < g1; ++k) {
-            const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+            const int deg = kTab ? 0 : taylor_degree<Real>(c, k, hw);
             Real br = 0, bi = 0;
             with_degree<Real>(deg, [&](auto Dc) {
 #pragma unroll 4
@@ -1253,7 +1296,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
                        sc[2 * T + tid], sc[3 * T + tid], br, bi);
             const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
             const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
-            const int deg = kF64 ? 0 : taylor_degree<Real>(c, k, hw);
+            const int deg = kTab ? 0 : taylor_degree<Real>(c, k, hw);
             with_degree<Real>(deg, [&](auto Dc) {
                 if constexpr (kF64) {
 #pragma unroll

@@ -290,8 +290,11 @@ def main():
     if not args.no_also:
         for cfg in ALSO:
             p2, ms2, st2 = timed(cfg, 3, 2, profile=True)
+            err2 = None
+            if rank == 0 and not args.no_cpu:
+                err2 = sampled_error(p2, X, Y, A, x, y, a, cfg["delta"], dev, n=4)
             also.append({"precision": cfg["precision"], "delta": cfg["delta"], "eps": cfg["eps"], "n_e": p2.n_e,
-                         "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2})
+                         "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2, "error": err2})
 
     # error of the headline result against the oracle's direct sum at sampled targets
     head_err = None

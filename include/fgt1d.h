@@ -60,14 +60,16 @@ typedef void* fgt1d_stream;              /* a cudaStream_t */
 #define FGT1D_ETOOLARGE 8     /* problem larger than the fixed scratch of fgt1d_execute_noalloc */
 
 /* plan flags */
-#define FGT1D_FP64 0u         /* every step in FP64 */
+#define FGT1D_FP64 0u         /* FP64 accuracy at every step (recurrences, gaps, carries in
+                                 FP64; each multiplier rounded once to FP64 from exact
+                                 partial sums formed partly on the FP32 pipe) */
 #define FGT1D_FP32 1u         /* bulk recurrences in FP32 complex, FP64 coordinate differences
                                  and inter-tile carries; requires eps >= 1e-6 */
 #define FGT1D_EXACT_SELF 2u   /* a source at exactly a target's coordinate contributes
                                  G(0) = 1 instead of S_n(0) (the paper's codes use S_n(0)) */
 #define FGT1D_F32X2 4u        /* recurrences in double-float (pairs of FP32, ~48-bit
-                                 significand) with FP64 tile carries: FP64-grade accuracy
-                                 without the FP64 pipe; gradients use the FP64 path */
+                                 significand) with FP64 tile carries, within ~32x the FP64
+                                 path's rounding; gradients use the FP64 path */
 
 #define FGT1D_MAX_TERMS 8     /* largest n_e a plan can hold */
 #define FGT1D_MAX_N 14        /* largest CF order n built in FP64 (Sec. 3.3) */

@@ -33,7 +33,7 @@ def soe_cf(n):
 class Plan:
     """A transform plan for bandwidth delta and accuracy eps (or a given SOE).
 
-    precision: "fp64" (every step in FP64), "fp32" (FP32-complex recurrences with
+    precision: "fp64" (FP64 accuracy at every step), "fp32" (FP32-complex recurrences with
     FP64 coordinate differences and inter-tile carries; eps >= 1e-6) or "f32x2"
     (double-float recurrences, FP64-grade accuracy; gradients run in FP64).
     exact_self: coincident source/target pairs contribute G(0) = 1 instead of S_n(0).

@@ -125,7 +125,7 @@ struct SweepArgs {
     TileDesc* bdesc;        // [max_tiles][n_e]
     uint32_t* tile_ctr;     // [2]
     uint32_t* status;
-    int reuse = 0;          // 1: the FP64 multiplier table holds a bound geometry's multipliers
+    int reuse = 0;          // 1: the multiplier table holds a bound geometry's multipliers
     int self = 0;           // 1: identical targets and sources (every point is both; FP64)
 };
 
@@ -140,9 +140,11 @@ cudaError_t launch_sweeps_f32(const SweepArgs& a, const SweepConsts& c, cudaStre
                               int shape);
 // Double-float sweeps (value channel only).
 cudaError_t launch_sweeps_df(const SweepArgs& a, const SweepConsts& c, cudaStream_t st, cudaEvent_t mid, int shape);
-// Fills the FP64 multiplier table of a bound geometry (one block per tile) in the
-// thread-interleaved layout of sweep tile shape `shape`.
-cudaError_t launch_fill_table(const SweepArgs& a, const SweepConsts& c, int shape, cudaStream_t st);
+// Fills the multiplier table of a bound geometry (one block per tile) in the
+// thread-interleaved layout of sweep tile shape `shape`: FP64 entries, or double-float
+// entries for the double-float sweeps.
+cudaError_t launch_fill_table(const SweepArgs& a, const SweepConsts& c, int shape, bool dfloat_entries,
+                              cudaStream_t st);
 // Geometry tag check before an apply: when *tag != expect, flags kStatusBadArg and sets
 // *total_tiles = 0 so that no sweep tile runs on an unbound workspace.
 cudaError_t launch_geometry_check(const uint64_t* tag, uint64_t expect, int64_t* total_tiles, uint32_t* status,

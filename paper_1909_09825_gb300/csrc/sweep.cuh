@@ -897,8 +897,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
 
     const int i0 = tid * R;
     const double zprev = s_zprev, zend = s_z[pad<R>(nvalid - 1)];
-    // multipliers read from a bound geometry's table (FP64 only): no gaps needed
-    const bool reuse = kF64 && !CO && a.reuse;
+    // multipliers read from a bound geometry's table (FP64, double-float): no gaps needed
+    const bool reuse = kTab && !CO && a.reuse;
     // gaps of my R points, warp-wide largest gap
     Real thr[R];
     uint32_t hw = 0;
@@ -976,12 +976,13 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 // this thread's R multipliers are slots r T + tid of the tile (interleaved table)
                 double2* __restrict__ mt = kTab ? a.mult + (int64_t)k * a.Ppad + base + tid : nullptr;
                 bool loaded = false;
-                if constexpr (kF64) {
+                if constexpr (kTab) {
                     if (reuse) {
 #pragma unroll 4
                         for (int r = 0; r < R; ++r) {
-                            const double2 m = i0 + r < nvalid ? mt[r * T] : make_double2(1.0, 0.0);
-                            cfma_ra<Real>(m.x, m.y, fr, fi, s_al[pad<R>(i0 + r)], fr, fi);
+                            Real mr = Real(1), mi = Real(0);
+                            if (i0 + r < nvalid) TableEntry<Real>::load(mt + r * T, mr, mi);
+                            cfma_ra<Real>(mr, mi, fr, fi, strength(r), fr, fi);
                         }
                         loaded = true;
                     }
@@ -1360,12 +1361,13 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     }
 }
 
-// The multiplier table of a bound geometry (FP64): exp(-tau_k s (z_p - z_{p-1})) for
+// The multiplier table of a bound geometry (entries of Real: FP64, or double-float
+// rounded from the FP64 value): exp(-tau_k s (z_p - z_{p-1})) for
 // every real point p of every item (1 at an item's first point), the values the forward
 // sweep would store, at the interleaved slot (i % sR) sT + i / sR of tile point i for
 // the sweeps' tile shape sT x sR.  One block per
 // 4096-point tile; thread t fills slots t, t + T, ... (coalesced stores).
-template <int T>
+template <int T, typename Real>
 __global__ void __launch_bounds__(T) k_fill_table(const SweepArgs a, const SweepConsts c, int sT, int sR) {
     __shared__ int s_item;
     const int tid = threadIdx.x;
@@ -1390,7 +1392,8 @@ __global__ void __launch_bounds__(T) k_fill_table(const SweepArgs a, const Sweep
             const bool hyb = hw <= c.theta_hyb_lim[k];
             with_degree<double>(taylor_degree<double>(c, k, hw),
                                 [&](auto Dc) { taylor<double>(c, k, Dc, th, mr, mi, hyb); });
-            if (i < nvalid) a.mult[(int64_t)k * a.Ppad + base + j] = make_double2(mr, mi);
+            if (i < nvalid)
+                TableEntry<Real>::store(a.mult + (int64_t)k * a.Ppad + base + j, to_real<Real>(mr), to_real<Real>(mi));
         }
     }
 }

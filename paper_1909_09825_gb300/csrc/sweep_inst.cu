@@ -38,9 +38,11 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_table(const SweepArgs& a, const SweepConsts& c, int shape, cudaStream_t st) {
+cudaError_t launch_fill_table(const SweepArgs& a, const SweepConsts& c, int shape, bool dfloat_entries,
+                              cudaStream_t st) {
     const int sT = shape == 1 ? Shape<1>::T : Shape<0>::T, sR = shape == 1 ? Shape<1>::R : Shape<0>::R;
-    k_fill_table<256><<<(unsigned)a.max_tiles, 256, 0, st>>>(a, c, sT, sR);
+    if (dfloat_entries) k_fill_table<256, dfloat><<<(unsigned)a.max_tiles, 256, 0, st>>>(a, c, sT, sR);
+    else k_fill_table<256, double><<<(unsigned)a.max_tiles, 256, 0, st>>>(a, c, sT, sR);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,8 @@ def test_geometry_argument_errors(L):
     assert b.value == n.value  # the bound state is the transform's workspace
     p32 = fgt.Plan(1e-3, 1e-6, precision="fp32")
     assert L.fgt1d_geometry_workspace_size(p32.handle, 1000, 2000, ctypes.byref(b)) == _lib.FGT1D_EUNSUPPORTED
+    pdf = fgt.Plan(1e-3, 1e-6, precision="f32x2")
+    assert L.fgt1d_geometry_workspace_size(pdf.handle, 1000, 2000, ctypes.byref(b)) == _lib.FGT1D_OK
     assert L.fgt1d_geometry_workspace_size(p64.handle, -1, 2000, ctypes.byref(b)) == _lib.FGT1D_EINVAL
     assert L.fgt1d_geometry_bind(p64.handle, None, 10, None, 10, None, 0, None) == _lib.FGT1D_EWORKSPACE
     assert L.fgt1d_geometry_apply(None, 10, 10, None, None, None, 0, None) == _lib.FGT1D_EINVAL

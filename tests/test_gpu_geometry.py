@@ -22,18 +22,22 @@ def _t(v, dev):
     return torch.from_numpy(np.ascontiguousarray(v)).to(dev)
 
 
+TOL = {"fp64": TOL_ARITH64, "f32x2": 32 * TOL_ARITH64}  # double-float: 2^-48 instead of 2^-53
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
 @pytest.mark.parametrize("M,N,delta", [(1, 1, 1e-3), (33, 65, 1e-2), (4097, 3000, 1e-3), (30001, 29999, 1e-5)])
-def test_apply_many_alphas_vs_recurrence(cuda, M, N, delta):
+def test_apply_many_alphas_vs_recurrence(cuda, M, N, delta, prec):
     x, y, a0 = inputs.uniform(M, N, seed=M + 3 * N)
     n, tau, W, En = soe_cf.plan_soe(1e-10)
-    plan = fgt.Plan(delta, soe=(tau, W))
+    plan = fgt.Plan(delta, soe=(tau, W), precision=prec)
     g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
     rng = np.random.default_rng(5)
     for rep in range(3):
         a = a0 if rep == 0 else rng.standard_normal(N)
         u = g.apply(_t(a, cuda)).cpu().numpy()
         ref = oracle.recurrence(x, y, a, delta, tau, W)
-        assert rel_inf(u, ref, a) <= TOL_ARITH64, rep
+        assert rel_inf(u, ref, a) <= TOL[prec], rep
 
 
 def test_apply_equals_transform(cuda):
@@ -44,16 +48,17 @@ def test_apply_equals_transform(cuda):
     assert rel_inf(u, gpu_transform(plan, x, y, a), a) <= TOL_ARITH64
 
 
-def test_apply_ties_and_exact_self(cuda):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_apply_ties_and_exact_self(cuda, prec):
     x, y, a = inputs.with_ties(6000, 5000, seed=12, n_distinct=300)
     delta = 1e-3
     n, tau, W, En = soe_cf.plan_soe(1e-8)
     for exact in (False, True):
-        plan = fgt.Plan(delta, soe=(tau, W), exact_self=exact)
+        plan = fgt.Plan(delta, soe=(tau, W), exact_self=exact, precision=prec)
         g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
         u = g.apply(_t(a, cuda)).cpu().numpy()
         ref = oracle.recurrence(x, y, a, delta, tau, W, exact_self=exact)
-        assert rel_inf(u, ref, a) <= TOL_ARITH64
+        assert rel_inf(u, ref, a) <= TOL[prec]
 
 
 @pytest.mark.parametrize("tile", [128, 256])
@@ -96,6 +101,12 @@ def test_apply_guards(cuda):
     # binding again restores the geometry
     g2 = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
     assert rel_inf(g2.apply(A).cpu().numpy(), u_ok, a) <= TOL_ARITH64
+    # the precision is part of the tag: an f32x2 plan on an FP64-bound workspace
+    dfp = fgt.Plan(1e-3, 1e-6, precision="f32x2")
+    assert _lib.lib().fgt1d_geometry_apply(dfp.handle, 3000, 2000, ctypes.c_void_p(A.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(g2.ws.data_ptr()),
+                                           g2.ws.numel(), st) == 0
+    assert _lib.lib().fgt1d_check(ctypes.c_void_p(g2.ws.data_ptr()), g2.ws.numel(), st) == _lib.FGT1D_EINVAL
     # FP32 plans have no table
     with pytest.raises(_lib.FGTError) as e:
         fgt.Geometry(fgt.Plan(1e-3, 1e-6, precision="fp32"), _t(x, cuda), _t(y, cuda))

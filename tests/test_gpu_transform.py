@@ -187,6 +187,23 @@ def test_f32x2_matches_fp64_path(cuda, delta):
     assert err <= TOL_ARITH64 / 10
 
 
+@pytest.mark.parametrize("delta", [100.0, 1.0, 1e-2, 1e-4, 1e-6])
+def test_fp64_multipliers_at_full_precision(cuda, delta):
+    """The FP64 path against the direct SOE sum (O2, compensated, no recurrence) relative
+    to max |u|.  At delta = 100 every multiplier is within 1e-5 of 1 and the recurrences
+    run over all 4e4 points with cancelling terms, so rounding in the multipliers shows:
+    the FP64 path stays below 5e-11 (measured 1.5e-11; the oracle's own FP64 recurrence
+    3.5e-11, double-float 1.8e-10), where multipliers good to only 2^-48 would not."""
+    x, y, a = inputs.uniform(20000, 20000, seed=47)
+    n, tau, W, En = soe_cf.plan_soe(1e-10)
+    u = gpu_transform(fgt.Plan(delta, soe=(tau, W)), x, y, a)
+    idx = np.arange(0, 20000, 50)
+    ref = oracle.soe_direct(x[idx], y, a, delta, tau, W)
+    err = np.max(np.abs(u[idx] - ref)) / np.max(np.abs(ref))
+    print("delta", delta, "fp64 vs direct SOE sum / max|u|", err)
+    assert err <= 5e-11
+
+
 def test_f32x2_mixture_and_ties(cuda):
     """Clustered points (gaps across many binades) and exact ties / signed zeros."""
     for x, y, a, delta in [(*inputs.mixture(30000, 30000, seed=9), 1e-6), (*inputs.with_ties(5000, 4000, seed=3), 1e-2)]:

@@ -734,31 +734,54 @@ template <>
 __device__ __forceinline__ dfloat gap_real<dfloat>(double a, double b, const Scale& sc) { return sc.df * gap_df(a, b); }
 
 // Stages the tile: coordinates, strengths (0 at targets) and target bits.  Points past
-// the end get z = 0, alpha = 0 and are not targets.
+// the end get z = 0, alpha = 0 and are not targets.  The loads go in chunks of kChunk
+// points per thread, all issued before any is used (keys and codes, then the strength
+// gathers they index), so a tile waits for two memory round trips per chunk instead of
+// two per point.
 template <typename Real, int T, int R>
 __device__ __forceinline__ void stage_tile(const SweepArgs& a, const uint64_t* __restrict__ keys,
                                            const uint32_t* __restrict__ vals, int64_t base, int nvalid,
                                            double* s_z, Real* s_al, uint32_t* s_tgt) {
     constexpr int TILE = T * R;
+    constexpr int kIter = TILE / T;  // points per thread
+    constexpr int kChunk = kIter < 8 ? kIter : 8;
+    static_assert(kIter % kChunk == 0, "whole chunks");
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int i = tid; i < TILE; i += T) {
-        double z = 0.0, al = 0.0;
-        bool tg = false;
-        if (i < nvalid) {
-            const int64_t p = base + i;
-            z = key_coord(keys[p]);
-            const uint32_t v = vals[p];
-            if ((int64_t)v < a.N) {
-                al = __ldg(&a.alpha[v]);
-                tg = a.self != 0;  // identical targets and sources: every point is both
-            } else {
-                tg = true;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kIter; c0 += kChunk) {
+        uint64_t kk[kChunk];
+        uint32_t vv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int i = (c0 + q) * T + tid;
+            kk[q] = 0;
+            vv[q] = 0xFFFFFFFFu;
+            if (i < nvalid) {
+                kk[q] = keys[base + i];
+                vv[q] = vals[base + i];
             }
         }
-        s_z[pad<R>(i)] = z;
-        s_al[pad<R>(i)] = to_real<Real>(al);
-        const unsigned b = __ballot_sync(0xffffffffu, tg);
-        if (lane == 0) s_tgt[i >> 5] = b;
+        double al[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int i = (c0 + q) * T + tid;
+            al[q] = (i < nvalid && (int64_t)vv[q] < a.N) ? __ldg(&a.alpha[vv[q]]) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int i = (c0 + q) * T + tid;
+            bool tg = false;
+            double z = 0.0;
+            if (i < nvalid) {
+                z = key_coord(kk[q]);
+                // a target, or any point when targets and sources are identical
+                tg = (int64_t)vv[q] >= a.N || a.self != 0;
+            }
+            s_z[pad<R>(i)] = z;
+            s_al[pad<R>(i)] = to_real<Real>(al[q]);
+            const unsigned b = __ballot_sync(0xffffffffu, tg);
+            if (lane == 0) s_tgt[i >> 5] = b;
+        }
     }
 }
 

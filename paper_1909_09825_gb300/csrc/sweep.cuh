@@ -914,8 +914,10 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
+    // the previous tile's last coordinate, loaded before the staging so that both overlap
+    const uint64_t kprev = (tid == 0 && !first) ? keys[base - 1] : 0ull;
     stage_tile<Real, T, R>(a, keys, vals, base, nvalid, s_z, s_al, s_tgt);
-    if (tid == 0) s_zprev = !first ? key_coord(keys[base - 1]) : 0.0;
+    if (tid == 0) s_zprev = !first ? key_coord(kprev) : 0.0;
     __syncthreads();
 
     const int i0 = tid * R;
@@ -1192,8 +1194,10 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
+    // the next tile's first coordinate, loaded before the staging so that both overlap
+    const uint64_t knext = (tid == 0 && has_next) ? keys[base + TILE] : 0ull;
     stage_tile<Real, T, R>(a, keys, vals, base, nvalid, s_z, s_al, s_tgt);
-    if (tid == 0) s_z[pad<R>(TILE)] = has_next ? key_coord(keys[base + TILE]) : 0.0;
+    if (tid == 0) s_z[pad<R>(TILE)] = has_next ? key_coord(knext) : 0.0;
     __syncthreads();
 
     const int i0 = tid * R;

@@ -173,16 +173,17 @@ int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double
  * for every merged point p and term k (step a4), all kept in the workspace;
  * fgt1d_geometry_apply then runs steps a3 and a5-a7 for a strength vector alpha[N]
  * (device) into u[M] (device, original target order), reading the multipliers from the
- * table: no sort and no exponential.  The workspace (fgt1d_geometry_workspace_size,
+ * table: no sort and no exponential.  FP32 plans keep the sorted points without a table
+ * (their sweeps form a multiplier in a few FP32 multiply-adds, cheaper than reading
+ * it): their apply skips the sort only.  The workspace (fgt1d_geometry_workspace_size,
  * 256-byte aligned) belongs to the geometry until it is bound again or used by another
  * call; apply must get the same plan, tile shape and sizes as the bind (the workspace
  * carries a tag of M, N, delta, the nodes, the tile shape (the table's layout) and the
  * precision (its entries); a mismatch or an unbound workspace runs nothing and
  * fgt1d_check returns FGT1D_EINVAL).  Both calls are stream-ordered and graph-capturable;
- * apply calls sharing a workspace must not overlap.  FP64 plans, and F32X2 plans (the
- * table then holds double-float entries rounded from the FP64 multipliers);
- * FGT1D_EXACT_SELF allowed.  FP32 plans, whose sweeps keep no table, return
- * FGT1D_EUNSUPPORTED.  Errors: FGT1D_EINVAL,
+ * apply calls sharing a workspace must not overlap.  Every precision: FP64, F32X2 (the
+ * table then holds double-float entries rounded from the FP64 multipliers) and FP32;
+ * FGT1D_EXACT_SELF allowed.  Errors: FGT1D_EINVAL,
  * FGT1D_EWORKSPACE, FGT1D_ECUDA; a NaN/Inf coordinate found by bind is reported by
  * fgt1d_check as FGT1D_ENONFINITE. */
 int fgt1d_geometry_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes);

@@ -580,14 +580,13 @@ uint64_t geometry_tag(const fgt1d_plan_s& p, int64_t M, int64_t N) {
     mix(p.tau_im, sizeof(double) * (size_t)p.n_e);
     const int shape = shape_index(p);  // the table layout follows the tile shape
     mix(&shape, sizeof(shape));
-    const unsigned df = p.flags & FGT1D_F32X2;  // and its entries the precision
-    mix(&df, sizeof(df));
+    const unsigned prec = p.flags & (FGT1D_F32X2 | FGT1D_FP32);  // and its entries the precision
+    mix(&prec, sizeof(prec));
     return h;
 }
 
 int geometry_checks(fgt1d_plan plan, int64_t M, int64_t N, void* ws, size_t ws_bytes, Layout& L) {
     if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
-    if (plan->flags & FGT1D_FP32) return FGT1D_EUNSUPPORTED;  // the FP32 sweeps keep no table
     L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
     if (M > 0 && N > 0) return ws_ok(ws, ws_bytes, L);
     return FGT1D_OK;
@@ -621,7 +620,10 @@ extern "C" int fgt1d_geometry_bind(fgt1d_plan plan, const double* x, int64_t M, 
     if (e == cudaSuccess) e = launch_sort(sa, st);
     SweepArgs w = sweep_args(nullptr, N, nullptr, nullptr, ws, L);
     SweepConsts c = make_consts(*plan);
-    if (e == cudaSuccess) e = launch_fill_table(w, c, shape_index(*plan), (plan->flags & FGT1D_F32X2) != 0, st);
+    // FP32 plans keep the sorted points only: their sweeps recompute a multiplier with a
+    // few FP32 multiply-adds, fewer cycles than reading a stored entry from HBM
+    if (e == cudaSuccess && !(plan->flags & FGT1D_FP32))
+        e = launch_fill_table(w, c, shape_index(*plan), (plan->flags & FGT1D_F32X2) != 0, st);
     if (e == cudaSuccess)
         e = launch_geometry_tag(reinterpret_cast<uint64_t*>(ws + L.header + kTagOffset), geometry_tag(*plan, M, N), st);
     return cuda_status(e);
@@ -649,11 +651,12 @@ extern "C" int fgt1d_geometry_apply(fgt1d_plan plan, int64_t M, int64_t N, const
         e = launch_geometry_check(reinterpret_cast<const uint64_t*>(ws + L.header + kTagOffset),
                                   geometry_tag(p, M, N), total_tiles, status, st);
     SweepArgs w = sweep_args(alpha, N, u, nullptr, ws, L);
-    w.reuse = 1;
+    w.reuse = (p.flags & FGT1D_FP32) ? 0 : 1;
     SweepConsts c = make_consts(p);
     if (e == cudaSuccess) {
-        e = (p.flags & FGT1D_F32X2) ? launch_sweeps_df(w, c, st, nullptr, shape_index(p))
-                                    : launch_sweeps_f64(w, c, st, nullptr, 1, shape_index(p));
+        if (p.flags & FGT1D_FP32) e = launch_sweeps_f32(w, c, st, nullptr, 1, shape_index(p));
+        else if (p.flags & FGT1D_F32X2) e = launch_sweeps_df(w, c, st, nullptr, shape_index(p));
+        else e = launch_sweeps_f64(w, c, st, nullptr, 1, shape_index(p));
     }
     if (e == cudaSuccess && (p.flags & FGT1D_EXACT_SELF)) {
         double* A = reinterpret_cast<double*>(ws + L.coinc);

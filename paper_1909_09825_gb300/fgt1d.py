@@ -302,7 +302,8 @@ class Geometry:
     """Fixed targets x and sources y bound once (fgt1d_geometry_bind: sorted merged
     points and the FP64 multiplier table kept on the device); apply() then evaluates
     the transform for any strength vector without sorting or exponentials.  Owns its
-    workspace.  FP64 and f32x2 plans (fp32 plans keep no multiplier table)."""
+    workspace.  fp64 and f32x2 plans store the table; fp32 plans keep the sorted points
+    only (their sweeps recompute each multiplier in a few FP32 multiply-adds)."""
 
     def __init__(self, plan, x, y, stream=None, sync_check=True):
         _dev(x, "x"), _dev(y, "y")

@@ -22,14 +22,16 @@ def _t(v, dev):
     return torch.from_numpy(np.ascontiguousarray(v)).to(dev)
 
 
-TOL = {"fp64": TOL_ARITH64, "f32x2": 32 * TOL_ARITH64}  # double-float: 2^-48 instead of 2^-53
+# double-float: 2^-48 instead of 2^-53; FP32: the 5e-6 arithmetic budget of the FP32 path
+TOL = {"fp64": TOL_ARITH64, "f32x2": 32 * TOL_ARITH64, "fp32": 5e-6}
+EPS = {"fp64": 1e-10, "f32x2": 1e-10, "fp32": 1e-6}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+@pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32"])
 @pytest.mark.parametrize("M,N,delta", [(1, 1, 1e-3), (33, 65, 1e-2), (4097, 3000, 1e-3), (30001, 29999, 1e-5)])
 def test_apply_many_alphas_vs_recurrence(cuda, M, N, delta, prec):
     x, y, a0 = inputs.uniform(M, N, seed=M + 3 * N)
-    n, tau, W, En = soe_cf.plan_soe(1e-10)
+    n, tau, W, En = soe_cf.plan_soe(EPS[prec])
     plan = fgt.Plan(delta, soe=(tau, W), precision=prec)
     g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
     rng = np.random.default_rng(5)
@@ -40,19 +42,36 @@ def test_apply_many_alphas_vs_recurrence(cuda, M, N, delta, prec):
         assert rel_inf(u, ref, a) <= TOL[prec], rep
 
 
-def test_apply_equals_transform(cuda):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_equals_transform(cuda, prec):
     x, y, a = inputs.mixture(50000, 40000, seed=7)
-    plan = fgt.Plan(1e-4, 1e-8)
+    plan = fgt.Plan(1e-4, 1e-8 if prec == "fp64" else 1e-6, precision=prec)
     g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
     u = g.apply(_t(a, cuda)).cpu().numpy()
-    assert rel_inf(u, gpu_transform(plan, x, y, a), a) <= TOL_ARITH64
+    # FP32: the same sweeps over the same sorted points; only the look-back order differs
+    assert rel_inf(u, gpu_transform(plan, x, y, a), a) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_apply_fp32_vs_direct(cuda):
+    """The FP32 apply against the direct Gauss sum at the FP32 path's bound 2 eps + 5e-6,
+    for several strength vectors on one bound mixture geometry."""
+    x, y, a0 = inputs.mixture(40000, 30000, seed=21)
+    plan = fgt.Plan(1e-4, 1e-6, precision="fp32")
+    g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
+    rng = np.random.default_rng(22)
+    idx = rng.choice(len(x), 200, replace=False)
+    for rep in range(3):
+        a = a0 if rep == 0 else rng.uniform(-1, 1, len(y))
+        u = g.apply(_t(a, cuda)).cpu().numpy()
+        ref = oracle.direct(x[idx], y, a, 1e-4)
+        assert np.max(np.abs(u[idx] - ref)) / np.abs(a).sum() <= 2 * 1e-6 + 5e-6, rep
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32"])
 def test_apply_ties_and_exact_self(cuda, prec):
     x, y, a = inputs.with_ties(6000, 5000, seed=12, n_distinct=300)
     delta = 1e-3
-    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    n, tau, W, En = soe_cf.plan_soe(EPS[prec] if prec == "fp32" else 1e-8)
     for exact in (False, True):
         plan = fgt.Plan(delta, soe=(tau, W), exact_self=exact, precision=prec)
         g = fgt.Geometry(plan, _t(x, cuda), _t(y, cuda))
@@ -107,7 +126,9 @@ def test_apply_guards(cuda):
                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(g2.ws.data_ptr()),
                                            g2.ws.numel(), st) == 0
     assert _lib.lib().fgt1d_check(ctypes.c_void_p(g2.ws.data_ptr()), g2.ws.numel(), st) == _lib.FGT1D_EINVAL
-    # FP32 plans have no table
-    with pytest.raises(_lib.FGTError) as e:
-        fgt.Geometry(fgt.Plan(1e-3, 1e-6, precision="fp32"), _t(x, cuda), _t(y, cuda))
-    assert e.value.code == _lib.FGT1D_EUNSUPPORTED
+    # and an FP32 plan (no table) on it too
+    p32 = fgt.Plan(1e-3, 1e-6, precision="fp32")
+    assert _lib.lib().fgt1d_geometry_apply(p32.handle, 3000, 2000, ctypes.c_void_p(A.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(g2.ws.data_ptr()),
+                                           g2.ws.numel(), st) == 0
+    assert _lib.lib().fgt1d_check(ctypes.c_void_p(g2.ws.data_ptr()), g2.ws.numel(), st) == _lib.FGT1D_EINVAL

@@ -237,9 +237,12 @@ int o3_recurrence(const double* x, int64_t M, const double* y, const double* alp
  * forward pass h+_i = beta_i + e_{i-1} h+_{i-1} (inclusive), backward pass
  * h-_i = e_i (beta_{i+1} + h-_{i+1}) (exclusive), u = Re sum_k W_k (h+ + h-), unpermute;
  * beta is alpha in sorted order and e_i = exp(-t_k (x_{i+1} - x_i) / sqrt(delta)) for
- * consecutive sorted points.  Returns 0 or the error of o3_sort_merged. */
+ * consecutive sorted points.  exact_self != 0 adds (1 - S_n(0)) times the strengths of
+ * all points at x_i (the point itself included), so that the self pair and every
+ * coincident pair get G(0) = 1 instead of S_n(0).  Returns 0 or the error of
+ * o3_sort_merged. */
 int o3_recurrence_self(const double* x, const double* alpha, int64_t N, double delta, int n_e, const double* tre,
-                       const double* tim, const double* wre, const double* wim, double* u) {
+                       const double* tim, const double* wre, const double* wim, int exact_self, double* u) {
     if (n_e < 1 || n_e > ORACLE_MAX_TERMS) return -3;
     int64_t* perm = (int64_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
     double* hre = (double*)calloc((size_t)(N > 0 ? N : 1) * n_e, sizeof(double));
@@ -281,6 +284,14 @@ int o3_recurrence_self(const double* x, const double* alpha, int64_t N, double d
         double acc = 0.0;
         for (int k = 0; k < n_e; ++k)
             acc += wre[k] * (hre[i * n_e + k] + Br[k]) - wim[k] * (him[i * n_e + k] + Bi[k]);
+        if (exact_self) {
+            /* the run of equal coordinates around sorted position i, both directions */
+            double zi = x[perm[i]], same = alpha[perm[i]], s0 = 0.0;
+            for (int64_t r = i - 1; r >= 0 && x[perm[r]] == zi; --r) same += alpha[perm[r]];
+            for (int64_t r = i + 1; r < N && x[perm[r]] == zi; ++r) same += alpha[perm[r]];
+            for (int k = 0; k < n_e; ++k) s0 += wre[k];
+            acc += (1.0 - s0) * same;
+        }
         u[perm[i]] = acc;
     }
     free(perm); free(hre); free(him);

@@ -38,7 +38,7 @@ def lib():
         L.o2_soe_direct.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, p, i32]
         L.o3_recurrence.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, i32, p, p]
         L.o3_recurrence.restype = i32
-        L.o3_recurrence_self.argtypes = [p, p, i64, d, i32, p, p, p, p, p]
+        L.o3_recurrence_self.argtypes = [p, p, i64, d, i32, p, p, p, p, i32, p]
         L.o3_recurrence_self.restype = i32
         L.o3_sort_merged.argtypes = [p, i64, p, i64, p]
         L.o3_sort_merged.restype = i32
@@ -98,14 +98,15 @@ def recurrence(x, y, alpha, delta, tau, W, exact_self=False, return_perm=False):
     return (u, perm) if return_perm else u
 
 
-def recurrence_self(x, alpha, delta, tau, W):
+def recurrence_self(x, alpha, delta, tau, W, exact_self=False):
     """O3 for identical targets and sources (Fig. 4.1): one sort of the N points,
-    inclusive forward and exclusive backward recurrences."""
+    inclusive forward and exclusive backward recurrences; exact_self gives the self
+    pair and every coincident pair G(0) = 1 instead of S_n(0)."""
     x, alpha = _f64(x), _f64(alpha)
     n, tr, ti, wr, wi = _soe(tau, W)
     u = np.empty(len(x))
     rc = lib().o3_recurrence_self(_ptr(x), _ptr(alpha), len(x), float(delta), n, _ptr(tr), _ptr(ti), _ptr(wr),
-                                  _ptr(wi), _ptr(u))
+                                  _ptr(wi), int(bool(exact_self)), _ptr(u))
     if rc != 0:
         raise ValueError("oracle self recurrence failed: %d" % rc)
     return u

@@ -82,6 +82,35 @@ def test_recurrence_self_equals_soe_direct_tiny(seed):
         assert np.max(np.abs(u - u2)) <= 1e-14 * np.abs(a).sum()
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_recurrence_self_exact_brute_force_tiny(seed):
+    """exact_self with identical points against brute force on tiny inputs with runs of
+    equal coordinates (signed zeros included): the kernel matrix is S_n(|x_i - x_j|)
+    except where x_i == x_j, where it is G(0) = 1."""
+    rng = np.random.default_rng(300 + seed)
+    N = int(rng.integers(1, 40))
+    vals = np.concatenate([[0.0, -0.0], rng.random(4)])
+    x = vals[rng.integers(0, 6, N)]
+    a = rng.standard_normal(N)
+    tau, W, _ = soe_cf.cf_soe(8)
+    delta = 0.05
+    d = np.abs(x[:, None] - x[None, :]) / np.sqrt(delta)
+    K = np.real(np.exp(-d[:, :, None] * tau[None, None, :]) @ W)
+    K[x[:, None] == x[None, :]] = 1.0
+    u = oracle.recurrence_self(x, a, delta, tau, W, exact_self=True)
+    assert np.max(np.abs(u - K @ a)) <= 1e-14 * np.abs(a).sum()
+
+
+def test_recurrence_self_exact_equals_general_exact():
+    """Identical-points exact_self against the general recurrence on (x, x) with
+    exact_self (sources before targets on ties), with ties."""
+    x, _, a = inputs.with_ties(3000, 3000, seed=31, n_distinct=200)
+    tau, W, _ = soe_cf.cf_soe(10)
+    u = oracle.recurrence_self(x, a[:len(x)], 1e-3, tau, W, exact_self=True)
+    u2 = oracle.recurrence(x, x, a[:len(x)], 1e-3, tau, W, exact_self=True)
+    assert np.max(np.abs(u - u2)) <= 1e-13 * np.abs(a[:len(x)]).sum()
+
+
 def test_recurrence_self_one_point():
     """N = 1: u = alpha S_n(0) = alpha Re sum_k W_k (the self weight of Fig. 4.1)."""
     tau, W, _ = soe_cf.cf_soe(8)

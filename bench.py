@@ -438,8 +438,14 @@ def identical_points(X, A, dev, world, stream):
         fgt.transform_self(plan, X, A_, out=U, workspace=ws)  # checks the device status
         ms_gen = _event_time(lambda: fgt.transform(plan, X, X, A_, out=U, workspace=ws, sync_check=False), 3, 2,
                              stream)
+        # with the exact self term (G(0) = 1 for the self pair and coincident pairs)
+        pex = fgt.Plan(1.0, eps, exact_self=True)
+        ms_ex = _event_time(lambda: fgt.transform_self(pex, X, A_, out=U, workspace=ws, sync_check=False), 3, 2,
+                            stream)
+        fgt.transform_self(pex, X, A_, out=U, workspace=ws)
         out.append({"points": "uniform", "eps": eps, "n_e": plan.n_e, "points_per_s": world * N / (ms_self * 1e-3),
-                     "ms": ms_self, "general_path_on_x_x_ms": ms_gen, "speedup": ms_gen / ms_self})
+                     "ms": ms_self, "general_path_on_x_x_ms": ms_gen, "speedup": ms_gen / ms_self,
+                     "exact_self_ms": ms_ex})
         del ws
         torch.cuda.empty_cache()
     # Sec. 5's second point set: Chebyshev points on [0, 1]

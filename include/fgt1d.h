@@ -159,9 +159,10 @@ int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const in
  * the N points x (device), strengths alpha[N] and output u[N] (device, original order).
  * The N points are sorted once (not 2N merged points); the forward state is inclusive
  * and the backward state exclusive, so the self term and every coincident pair get
- * S_n(0) as in Fig. 4.1.  Workspace: fgt1d_self_workspace_size.  FP64 plans without
- * FGT1D_EXACT_SELF (others return FGT1D_EUNSUPPORTED).  N = 0 is a no-op.  Errors as
- * fgt1d_execute. */
+ * S_n(0) as in Fig. 4.1; with FGT1D_EXACT_SELF they get G(0) = 1 (each u_i gains
+ * (1 - S_n(0)) times the total strength of the points at exactly x_i, itself included).
+ * Workspace: fgt1d_self_workspace_size.  FP64 plans (FP32 and F32X2 plans return
+ * FGT1D_EUNSUPPORTED).  N = 0 is a no-op.  Errors as fgt1d_execute. */
 int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes);
 int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,
                        void* workspace, size_t ws_bytes, fgt1d_stream stream);

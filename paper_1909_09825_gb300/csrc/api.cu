@@ -536,7 +536,7 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
 // ---- identical targets and sources --------------------------------------------------------
 extern "C" int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes) {
     if (!plan || !bytes || !sizes_ok(0, N)) return FGT1D_EINVAL;
-    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2 | FGT1D_EXACT_SELF)) return FGT1D_EUNSUPPORTED;
+    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) return FGT1D_EUNSUPPORTED;
     *bytes = make_layout(0, N, 1, plan->n_e, plan->flags, true, false).total;
     return FGT1D_OK;
 }
@@ -544,15 +544,30 @@ extern "C" int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* byt
 extern "C" int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,
                                   void* workspace, size_t ws_bytes, fgt1d_stream stream) {
     if (!plan || !sizes_ok(0, N)) return FGT1D_EINVAL;
-    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2 | FGT1D_EXACT_SELF)) return FGT1D_EUNSUPPORTED;
+    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) return FGT1D_EUNSUPPORTED;
     if (N == 0) return FGT1D_OK;
     if (!x || !alpha || !u) return FGT1D_EINVAL;
     Layout L = make_layout(0, N, 1, plan->n_e, plan->flags, true, false);
     int r = ws_ok(workspace, ws_bytes, L);
     if (r) return r;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the N points are merged once, as sources; the sweeps treat each as a target too
-    return run_pipeline(*plan, nullptr, 0, x, alpha, N, ItemSource(), u, nullptr, 1, nullptr,
-                        static_cast<char*>(workspace), L, static_cast<cudaStream_t>(stream), nullptr, true);
+    r = run_pipeline(*plan, nullptr, 0, x, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, nullptr, true);
+    if (r || !(plan->flags & FGT1D_EXACT_SELF)) return r;
+    // exact self term: add (1 - S_n(0)) times the total strength of each point's run of
+    // equal coordinates (the point itself included).  The coincidence sweep leaves the
+    // running run sums in sorted order over the forward partial sums, which are spent.
+    double* F = reinterpret_cast<double*>(ws + L.fwd);
+    SweepArgs w = sweep_args(alpha, N, F, nullptr, ws, L);
+    w.self = 1;
+    cudaError_t e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_coincidence(w, make_consts(*plan), st);
+    double s0 = 0.0;
+    for (int k = 0; k < plan->n_e; ++k) s0 += plan->w_re[k];
+    if (e == cudaSuccess) e = launch_self_exact(w, F, N, 1.0 - s0, u, st);
+    return cuda_status(e);
 }
 
 // ---- fixed geometry: bind once, apply many strength vectors ------------------------------

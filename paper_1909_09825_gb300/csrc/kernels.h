@@ -151,8 +151,13 @@ cudaError_t launch_geometry_check(const uint64_t* tag, uint64_t expect, int64_t*
                                   cudaStream_t st);
 cudaError_t launch_geometry_tag(uint64_t* tag, uint64_t value, cudaStream_t st);
 // Coincidence sums: u[i] = sum of alpha over the sources at exactly the coordinate of
-// target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).
+// target i (one forward scan with multiplier 1 on zero gaps and 0 otherwise).  With
+// identical points (a.self) u[p] is, per sorted position p, the sum over the points of
+// p's run of equal coordinates up to p.
 cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
+// Identical points: u[point at sorted position p] += cf * F[last position of p's run of
+// equal coordinates], F from launch_coincidence (the run's total strength).
+cudaError_t launch_self_exact(const SweepArgs& a, const double* F, int64_t n, double cf, double* u, cudaStream_t st);
 
 // fgt1d_execute on a caller-given workspace (checked against the layout size)
 int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,

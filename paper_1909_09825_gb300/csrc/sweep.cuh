@@ -910,7 +910,9 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     const int nvalid = (int)min((int64_t)TILE, itm.nsrc + itm.ntgt - local);
     const bool first = local == 0;
     const double s = itm.s;
-    const Scale sc = make_scale<Real>(s);
+    // the coincidence sweep compares gaps with zero: unscaled, so that no gap between
+    // distinct coordinates underflows
+    const Scale sc = make_scale<Real>(CO ? 1.0 : s);
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
@@ -1138,8 +1140,10 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
         __syncthreads();
     }
     if constexpr (CO) {
+        // per target in target order; with identical points, per point in sorted order
         for (int i = tid; i < nvalid; i += T)
-            if ((s_tgt[i >> 5] >> (i & 31)) & 1u) a.u[(int64_t)vals[base + i] - a.N] = real_to_f64<Real>(s_al[pad<R>(i)]);
+            if ((s_tgt[i >> 5] >> (i & 31)) & 1u)
+                a.u[a.self ? base + i : (int64_t)vals[base + i] - a.N] = real_to_f64<Real>(s_al[pad<R>(i)]);
     } else {
         for (int i = tid; i < nvalid; i += T) {
             if constexpr ((EV & 1) != 0) static_cast<Real*>(a.fwd)[base + i] = s_al[pad<R>(i)];

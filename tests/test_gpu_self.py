@@ -75,9 +75,46 @@ def test_self_large_vs_direct(cuda):
     assert rel_inf(u[idx], oracle.direct(x[idx], x, a, 1.0, nthreads=0), a) <= 2e-8 + 1e-13
 
 
+@pytest.mark.parametrize("n_distinct", [40, 3])
+def test_self_exact_vs_oracle(cuda, n_distinct):
+    """exact_self with identical points: runs of equal coordinates (signed zeros
+    included; with 3 distinct values every run spans many tiles) get G(0) = 1."""
+    x, _, a = inputs.with_ties(9000, 9000, seed=14, n_distinct=n_distinct)
+    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    for delta in (1e-2, 1.0):
+        plan = fgt.Plan(delta, soe=(tau, W), exact_self=True)
+        u = _self(plan, x, a, cuda)
+        assert rel_inf(u, oracle.recurrence_self(x, a, delta, tau, W, exact_self=True), a) <= TOL_ARITH64
+
+
+@pytest.mark.parametrize("N", [1, 4097, 30001])
+def test_self_exact_distinct_points(cuda, N):
+    """Distinct points: exact_self adds (1 - S_n(0)) alpha_i, the self pair only."""
+    x, _, _ = inputs.uniform(N, 1, seed=N + 5)
+    a = np.random.default_rng(N).standard_normal(N)
+    n, tau, W, En = soe_cf.plan_soe(1e-6)
+    plan = fgt.Plan(1e-3, soe=(tau, W), exact_self=True)
+    u = _self(plan, x, a, cuda)
+    assert rel_inf(u, oracle.recurrence_self(x, a, 1e-3, tau, W, exact_self=True), a) <= TOL_ARITH64
+    u0 = _self(fgt.Plan(1e-3, soe=(tau, W)), x, a, cuda)
+    assert rel_inf(u - u0, (1 - np.sum(W.real)) * a, a) <= TOL_ARITH64
+
+
+def test_self_exact_vs_direct(cuda):
+    """Against the direct Gauss sum (G(0) = 1 for the self pair) on a mixture with
+    duplicated points, at the 2 eps + 1e-13 bound."""
+    x, _, _ = inputs.mixture(20000, 1, seed=15)
+    x[10000:12000] = x[:2000]  # coincident pairs
+    a = np.random.default_rng(16).standard_normal(20000)
+    plan = fgt.Plan(1e-4, 1e-8, exact_self=True)
+    u = _self(plan, x, a, cuda)
+    idx = np.concatenate([np.arange(0, 20000, 331), np.arange(10000, 10040)])
+    assert rel_inf(u[idx], oracle.direct(x[idx], x, a, 1e-4), a) <= 2e-8 + 1e-13
+
+
 def test_self_unsupported_plans(cuda):
     x = torch.rand(100, dtype=torch.float64, device=cuda)
-    for plan in (fgt.Plan(1e-3, 1e-6, precision="fp32"), fgt.Plan(1e-3, 1e-6, exact_self=True)):
+    for plan in (fgt.Plan(1e-3, 1e-6, precision="fp32"), fgt.Plan(1e-3, 1e-6, precision="f32x2")):
         with pytest.raises(_lib.FGTError) as e:
             fgt.transform_self(plan, x, x)
         assert e.value.code == _lib.FGT1D_EUNSUPPORTED

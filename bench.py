@@ -305,9 +305,10 @@ def main():
     if not args.no_also:
         extra["geometry_reuse"] = geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args)
         extra["identical_points"] = identical_points(X, A, dev, world, stream)
+        extra["presorted"] = presorted(plan, X, Y, A, x, y, a, dev, world, stream, rank == 0 and not args.no_cpu)
         extra["precision_split"] = precision_split(args, dev, world, P)
         extra["differentiation"] = differentiation(dev, world)
-        extra["batched"] = batched(dev, world)
+        extra["batched"] = batched(dev, world, check=rank == 0 and not args.no_cpu)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -420,6 +421,51 @@ def geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args):
                                "table_bytes_per_point": 2 * 16 * n_e}}
 
 
+def presorted(plan, X, Y, A, x, y, a, dev, world, stream, check):
+    """Sec. 5's pre-sorted points: the headline targets and sources, each sorted
+    ascending (the strengths kept in place), through the same transform; the sort step
+    detects the presorted runs and merges them instead of running the digit passes.
+    Stage times from CUDA events recorded inside the call."""
+    import torch
+    from paper_1909_09825_gb300 import _lib
+    XS, YS = torch.sort(X).values, torch.sort(Y).values
+    M, N = X.numel(), Y.numel()
+    U = torch.empty(M, dtype=torch.float64, device=dev)
+    buf = torch.empty(plan.workspace_size(M, N), dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    arr = None
+
+    def run():
+        nonlocal arr
+        for e in ev:
+            e.record(stream)
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in ev])
+        _lib.check(_lib.lib().fgt1d_execute_profiled(
+            plan.handle, ctypes.c_void_p(XS.data_ptr()), M, ctypes.c_void_p(YS.data_ptr()),
+            ctypes.c_void_p(A.data_ptr()), N, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
+            buf.numel(), ctypes.c_void_p(stream.cuda_stream), arr), "execute_profiled")
+
+    ms = _event_time(run, 5, 3, stream)
+    st = [ev[i].elapsed_time(ev[i + 1]) for i in range(3)]
+    _lib.check(_lib.lib().fgt1d_check(ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                      ctypes.c_void_p(stream.cuda_stream)), "presorted (device status)")
+    err = None
+    if check:
+        from oracle import oracle
+        xs, ys = np.sort(x), np.sort(y)
+        idx = np.random.default_rng(19).choice(M, 8, replace=False)
+        ug = U[torch.from_numpy(idx).to(dev)].cpu().numpy()
+        ref = oracle.direct(xs[idx], ys, a, plan.delta, nthreads=0)
+        err = float(np.max(np.abs(ug - ref)) / np.abs(a).sum())
+    del XS, YS, U, buf
+    torch.cuda.empty_cache()
+    return {"workload": "headline x and y each sorted ascending (alpha in place), delta=%g, eps=%g, FP64"
+                        % (plan.delta, HEAD["eps"]),
+            "points_per_s": world * (M + N) / (ms * 1e-3), "ms": ms,
+            "stages_last_step": {"sort_ms": st[0], "fwd_sweep_ms": st[1], "bwd_sweep_ms": st[2]},
+            "error_vs_direct": err}
+
+
 def identical_points(X, A, dev, world, stream):
     """Fig. 4.1's case (targets = sources, the shape of Table 5.1: uniform points,
     delta = 1): the N = 2^26 headline targets with their strengths, one sort of N
@@ -456,8 +502,8 @@ def identical_points(X, A, dev, world, stream):
     ws = fgt.Workspace(dev)
     ms_c = _event_time(lambda: fgt.transform_self(plan, XC, A_, out=U, workspace=ws, sync_check=False), 3, 3, stream)
     fgt.transform_self(plan, XC, A_, out=U, workspace=ws)
-    out.append({"points": "chebyshev", "eps": 1e-6, "n_e": plan.n_e, "points_per_s": world * N / (ms_c * 1e-3),
-                "ms": ms_c})
+    out.append({"points": "chebyshev (generated in increasing order: the sort is one merge)", "eps": 1e-6,
+                "n_e": plan.n_e, "points_per_s": world * N / (ms_c * 1e-3), "ms": ms_c})
     del ws, XC
     torch.cuda.empty_cache()
     return {"workload": "N=2^%d uniform (Table 5.1's shape) or Chebyshev points on [0,1] as targets and sources, "
@@ -527,9 +573,11 @@ def differentiation(dev, world, log2=24):
             "backward_ms": ms_fb - ms_f}
 
 
-def batched(dev, world, B=4096):
+def batched(dev, world, B=4096, check=True):
     """B = 4096 transforms, M_b = N_b log-uniform in [1e2, 1e6], delta_b log-uniform in
-    [1e-6, 1e-1], eps = 1e-6 FP64, one pass of the kernels captured in a CUDA graph."""
+    [1e-6, 1e-1], eps = 1e-6 FP64, one pass of the kernels captured in a CUDA graph.
+    With check, 64 sampled items (4 sampled targets each) against the oracle's direct
+    Gauss sum over the item's sources."""
     import torch
     import paper_1909_09825_gb300 as fgt
     from paper_1909_09825_gb300 import inputs
@@ -548,12 +596,30 @@ def batched(dev, world, B=4096):
             fgt.transform_batched(plan, XO, YO, X, Y, A, delta=D, out=out, workspace=ws, stream=s, sync_check=False)
     torch.cuda.current_stream(dev).wait_stream(s)
     ms = _event_time(g.replay, 3, 2, torch.cuda.current_stream(dev))
+    err = None
+    if check:
+        from oracle import oracle
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(23)
+        off = XO.cpu().numpy()
+        dl = D.cpu().numpy()
+        worst = 0.0
+        for b in np.sort(rng.choice(B, 64, replace=False)):
+            lo, hi = int(off[b]), int(off[b + 1])
+            xs, ys, al = (t[lo:hi].cpu().numpy() for t in (X, Y, A))
+            idx = rng.choice(hi - lo, min(4, hi - lo), replace=False)
+            ref = oracle.direct(xs[idx], ys, al, float(dl[b]), nthreads=0)
+            ug = out[lo:hi].cpu().numpy()[idx]
+            worst = max(worst, float(np.max(np.abs(ug - ref)) / np.abs(al).sum()))
+        err = {"max_abs_err_over_sum_abs_alpha": worst, "sampled_items": 64, "targets_per_item": 4,
+               "reference": "oracle direct FP64 sum over the item's sources"}
     del XO, YO, D, X, Y, A, out, ws, g
     torch.cuda.empty_cache()
     return {"workload": "B=%d items, M_b=N_b=round(10^U(2,6)), delta_b=10^U(-6,-1), uniform x,y, alpha ~ N(0,1), "
                         "eps=1e-6 FP64 (n_e=%d), CUDA graph replay" % (B, plan.n_e),
             "points": P, "value": world * P / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
-            "tile_threads": plan.tile_threads, "autotune_ms": {str(k): v for k, v in tune.items() if k != "chosen"}}
+            "tile_threads": plan.tile_threads, "autotune_ms": {str(k): v for k, v in tune.items() if k != "chosen"},
+            "error": err}
 
 
 def _kernel_source_hash():

@@ -67,7 +67,10 @@ struct SortPlan {
     int32_t dst[kSortDigits];
     int32_t final_buf;          // buffer (0 = A, 1 = B) that holds the sorted keys/indices
     uint32_t active_mask;       // bit d: some item has more than one populated bucket in digit d
+    uint32_t unsorted;          // some item's sources or targets are not in non-decreasing order
+    uint32_t merge;             // 1: every run is presorted, the sort is one merge into buffer A
 };
+static_assert(128 + sizeof(SortPlan) <= 256, "the sort plan sits in the workspace header");
 
 struct SortArgs {
     const double* x;

@@ -15,6 +15,11 @@
 // keys and merged indices out through a shared-memory reorder so that every bucket
 // run is written contiguously.  The pass plan lives on the device, so the whole sort
 // is launched without a host round trip (and can be captured in a CUDA graph).
+//
+// Presorted inputs (Sec. 5's pre-sorted points; its Chebyshev points "sort in much less
+// time"): the histogram pass also checks that every item's sources and targets are each
+// in non-decreasing key order; when they are, the plan runs no digit pass and one merge
+// kernel writes the stable merged order (sources first on equal keys) instead.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -180,6 +185,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
         }
         __syncthreads();
     };
+    bool unsorted = false;
     for (int64_t t = t0; t < t1; ++t) {
         if (threadIdx.x == 0) s_item = item_of_tile(a.items, a.B, t);
         __syncthreads();
@@ -193,9 +199,22 @@ __global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
 #pragma unroll
         for (int d = 0; d < kSortDigits; ++d) { last[d] = 0; run[d] = 0; }
         for (int e = threadIdx.x; e < kTile; e += blockDim.x) {
+            // presorted check: the key before this one in the same run (sources or
+            // targets of this item), from the lane below or, for lane 0, from memory (that
+            // load is issued next to the point's own)
+            const int64_t l = t * kTile + e - it.start;
+            const bool chk = l > 0 && l != it.nsrc && l < it.nsrc + it.ntgt;
+            double cprev = 0.0;
+            if (chk && (threadIdx.x & 31) == 0)
+                cprev = l < it.nsrc ? a.y[it.y_off + l - 1] : a.x[it.x_off + (l - it.nsrc) - 1];
             uint64_t k;
             uint32_t v;
             merged_point(a, it, t * kTile + e, k, v, bad);
+            uint64_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+            if (chk) {
+                if ((threadIdx.x & 31) == 0) kp = coord_key(cprev);
+                unsorted |= kp > k;
+            }
 #pragma unroll
             for (int d = 0; d < kSortDigits; ++d) {
                 const uint32_t dg = (uint32_t)(k >> (8 * d)) & 255u;
@@ -214,6 +233,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
     }
     if (cur >= 0) flush(cur);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, kStatusNonFinite);
+    if (__any_sync(0xffffffffu, unsorted) && (threadIdx.x & 31) == 0) atomicOr(&a.plan->unsorted, 1u);
 }
 
 // ---- per-item bucket starts and the digits that need a pass (one block per item) ----------
@@ -247,6 +267,11 @@ __global__ void k_sort_chain(SortPlan* plan) {
         plan->active[d] = 0;
         plan->src[d] = 0;
         plan->dst[d] = 0;
+    }
+    plan->merge = plan->unsorted ? 0u : 1u;
+    if (plan->merge) {  // presorted runs: no digit pass, k_sort_merge writes buffer A
+        plan->final_buf = 0;
+        return;
     }
     for (int d = 0; d < kSortDigits; ++d) {
         if (!((mask >> d) & 1u)) continue;
@@ -456,6 +481,110 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, kStatusNonFinite);
 }
 
+// ---- presorted runs: one merge -------------------------------------------------------
+constexpr int kMergeIPT = kSortTile / kSortThreads;  // merged outputs per thread
+
+struct MergeSmem {
+    uint64_t key[kSortTile];
+    uint32_t val[kSortTile];
+};
+
+// Number of sources among the first d merged points of runs ys[ns], xs[nt] (each
+// non-decreasing; a source goes first on equal keys): the first i in [max(0, d - nt),
+// min(d, ns)) with ys[i] > xs[d - 1 - i], or min(d, ns) if there is none.  The warp tests
+// 32 evenly spaced candidates per step (the predicate is monotone: true, then false), so
+// the range shrinks 32-fold per step; every lane returns the same value.
+template <typename KY, typename KX>
+__device__ int64_t merge_split_warp(int64_t d, int64_t ns, int64_t nt, KY ky, KX kx) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = max((int64_t)0, d - nt), hi = min(d, ns);
+    while (lo < hi) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t i = lo + (int64_t)lane * step;
+        const bool p = i < hi && ky(i) <= kx(d - 1 - i);
+        const int c = __popc(__ballot_sync(0xffffffffu, p));
+        if (c == 0) break;  // the first candidate (lo) already fails
+        const int64_t nhi = min(hi, lo + (int64_t)c * step);
+        lo += (int64_t)(c - 1) * step + 1;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// One block per 4096-position tile of an item: two warps find where the tile starts and
+// ends on the merge path, the block stages the tile's sources and targets in shared
+// memory, each thread merges 16 consecutive outputs from its own split (a binary search
+// in shared memory), and the tile goes out through shared memory, coalesced.  Positions
+// past the item's points get the padding key and code, as in the digit passes.
+__global__ void __launch_bounds__(kSortThreads) k_sort_merge(SortArgs a) {
+    if (!a.plan->merge) return;
+    const int64_t tile = blockIdx.x;
+    if (tile >= *a.total_tiles) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MergeSmem& sm = *reinterpret_cast<MergeSmem*>(smem_raw);
+    __shared__ int s_item;
+    __shared__ int64_t s_split[2];
+    const int tid = threadIdx.x, w = tid >> 5;
+    if (tid == 0) s_item = item_of_tile(a.items, a.B, tile);
+    __syncthreads();
+    const Item it = a.items[s_item];
+    const int64_t ns = it.nsrc, nt = it.ntgt, nreal = ns + nt;
+    const int64_t d0 = min(tile * kSortTile - it.start, nreal), d1 = min(d0 + kSortTile, nreal);
+    const double* __restrict__ ys = ns > 0 ? a.y + it.y_off : nullptr;  // no sources: never read
+    const double* __restrict__ xs = nt > 0 ? a.x + it.x_off : nullptr;  // no targets: never read
+    auto ky = [&](int64_t i) { return coord_key(ys[i]); };
+    auto kx = [&](int64_t j) { return coord_key(xs[j]); };
+    if (w < 2) {
+        const int64_t sp = merge_split_warp(w == 0 ? d0 : d1, ns, nt, ky, kx);
+        if ((tid & 31) == 0) s_split[w] = sp;
+    }
+    __syncthreads();
+    const int64_t i0 = s_split[0], j0 = d0 - s_split[0];
+    const int nsl = (int)(s_split[1] - i0), nl = (int)(d1 - d0), ntl = nl - nsl;
+    for (int q = tid; q < nl; q += kSortThreads) sm.key[q] = q < nsl ? ky(i0 + q) : kx(j0 + (q - nsl));
+    __syncthreads();
+    uint64_t ok[kMergeIPT];
+    uint32_t ov[kMergeIPT];
+    const int dd = tid * kMergeIPT;
+    {
+        int lo = max(0, dd - ntl), hi = min(dd, nsl);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.key[mid] <= sm.key[nsl + dd - 1 - mid]) lo = mid + 1;
+            else hi = mid;
+        }
+        int ia = lo, ib = dd - lo;
+#pragma unroll
+        for (int q = 0; q < kMergeIPT; ++q) {
+            ok[q] = ~0ull;
+            ov[q] = 0xFFFFFFFFu;
+            if (dd + q < nl) {
+                if (ia < nsl && (ib >= ntl || sm.key[ia] <= sm.key[nsl + ib])) {
+                    ok[q] = sm.key[ia];
+                    ov[q] = (uint32_t)(it.y_off + i0 + ia);
+                    ++ia;
+                } else {
+                    ok[q] = sm.key[nsl + ib];
+                    ov[q] = (uint32_t)(a.N + it.x_off + j0 + ib);
+                    ++ib;
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMergeIPT; ++q) {
+        sm.key[dd + q] = ok[q];
+        sm.val[dd + q] = ov[q];
+    }
+    __syncthreads();
+    const int64_t base = tile * kSortTile;
+    for (int q = tid; q < kSortTile; q += kSortThreads) {
+        a.keysA[base + q] = sm.key[q];
+        a.valsA[base + q] = sm.val[q];
+    }
+}
+
 size_t sort_pass_smem() { return sizeof(SortSmem); }
 
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
@@ -469,6 +598,9 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
     k_sort_chain<<<1, 1, 0, st>>>(a.plan);
     for (int d = 0; d < kSortDigits; ++d)
         k_sort_pass<<<(unsigned)a.max_tiles, kSortThreads, sizeof(SortSmem), st>>>(a, d);
+    e = cudaFuncSetAttribute(k_sort_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
+    if (e != cudaSuccess) return e;
+    k_sort_merge<<<(unsigned)a.max_tiles, kSortThreads, sizeof(MergeSmem), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -84,10 +84,11 @@ def with_ties(M, N, seed=0, n_distinct=64):
 
 def chebyshev(N, seed=0, alpha="normal"):
     """The paper's second point set (Sec. 5): N Chebyshev points mapped to [0, 1],
-    x_i = (1 + cos(pi (2 i + 1) / (2 N))) / 2 (in decreasing order, clustered at both
-    ends), with seeded strengths alpha ~ N(0, 1)."""
+    x_i = (1 - cos(pi (2 i + 1) / (2 N))) / 2 = sin^2(pi (2 i + 1) / (4 N)) (the second
+    form has no cancellation near 0), in increasing order as a grid generator produces
+    them, clustered at both ends, with seeded strengths alpha ~ N(0, 1)."""
     rng = np.random.default_rng(seed)
-    x = 0.5 * (1.0 + np.cos(np.pi * (2.0 * np.arange(N) + 1.0) / (2.0 * N)))
+    x = np.sin(np.pi * (2.0 * np.arange(N) + 1.0) / (4.0 * N)) ** 2
     return x, _alpha(rng, N, alpha)
 
 

@@ -162,3 +162,24 @@ def test_batched_bad_items(cuda):
     with pytest.raises(_lib.FGTError) as e:
         _run(plan, bad, cuda)
     assert e.value.code == _lib.FGT1D_EINVAL
+
+
+def test_batched_presorted_items(cuda):
+    """Every item's sources and targets presorted: one merge for the whole batch."""
+    rng = np.random.default_rng(20)
+    B = 30
+    sx = rng.integers(0, 9000, B)
+    sy = rng.integers(0, 9000, B)
+    x_off, y_off, d, x, y, a = _batch(sx, sy, 10.0 ** rng.uniform(-5, -2, B), 21)
+    for i in range(B):
+        x[x_off[i]:x_off[i + 1]] = np.sort(x[x_off[i]:x_off[i + 1]])
+        y[y_off[i]:y_off[i + 1]] = np.sort(y[y_off[i]:y_off[i + 1]])
+    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    plan = fgt.Plan(1.0, soe=(tau, W))
+    u = _run(plan, (x_off, y_off, d, x, y, a), cuda)
+    for i in range(B):
+        xs, ys, al = x[x_off[i]:x_off[i + 1]], y[y_off[i]:y_off[i + 1]], a[y_off[i]:y_off[i + 1]]
+        if len(xs) == 0 or len(ys) == 0:
+            continue
+        ref = oracle.recurrence(xs, ys, al, d[i], tau, W)
+        assert np.max(np.abs(u[x_off[i]:x_off[i + 1]] - ref)) / np.abs(al).sum() <= TOL_ARITH64, i

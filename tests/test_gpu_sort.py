@@ -39,3 +39,38 @@ def test_perm_all_equal(cuda):
 def test_perm_mixture(cuda):
     x, y, _ = inputs.mixture(300000, 200000, seed=4)
     assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+
+
+def _presorted(M, N, seed, n_distinct=None):
+    rng = np.random.default_rng(seed)
+    if n_distinct:
+        vals = np.concatenate([[0.0, -0.0, -0.25], rng.random(n_distinct - 3)])
+        x, y = vals[rng.integers(0, n_distinct, M)], vals[rng.integers(0, n_distinct, N)]
+    else:
+        x, y = rng.random(M), rng.random(N)
+    return np.sort(x, kind="stable"), np.sort(y, kind="stable")
+
+
+@pytest.mark.parametrize("M,N,nd", [(1, 1, None), (0, 5000, None), (5000, 0, 7), (4096, 4096, None),
+                                    (4097, 12289, 5), (30001, 20000, 64), (100000, 3, None), (1 << 20, 1 << 19, None)])
+def test_perm_presorted(cuda, M, N, nd):
+    """Sources and targets each presorted (ties and signed zeros included): the sort is
+    one merge, bit-exact against the oracle's stable sort."""
+    x, y = _presorted(M, N, M + 7 * N, nd)
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+
+
+@pytest.mark.parametrize("where", ["x_lane0", "x_tile_start", "y_last", "x_only_sorted"])
+def test_perm_almost_presorted(cuda, where):
+    """One inversion (at a warp's first lane, at a tile start, at the last source) or one
+    unsorted run: the digit passes run, still bit-exact."""
+    x, y = _presorted(20000, 4096, 11)
+    if where == "x_lane0":
+        x[[31, 32]] = x[[32, 31]]       # merged position 4096 + 32: lane 0 of a warp
+    elif where == "x_tile_start":
+        x[[4095, 4096]] = x[[4096, 4095]]  # merged position 8192: first point of a tile
+    elif where == "y_last":
+        y[[4094, 4095]] = y[[4095, 4094]]
+    else:
+        y = np.random.default_rng(12).random(4096)
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))

@@ -317,3 +317,15 @@ def test_exact_self_term(cuda):
     plan2 = fgt.Plan(delta, 1e-8, exact_self=True)
     u2 = gpu_transform(plan2, x, y, a)
     assert rel_inf(u2, oracle.direct(x, y, a, delta), a) <= 2e-8 + 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_presorted_inputs_vs_recurrence(cuda, prec):
+    """Presorted targets and sources (Sec. 5's pre-sorted points: the sort is one merge)."""
+    x, y, a = inputs.uniform(30001, 25000, seed=41)
+    x, y = np.sort(x), np.sort(y)
+    delta = 1e-4
+    plan, tau, W = oracle_soe_plan(delta, 1e-6 if prec == "fp32" else 1e-10, precision=prec)
+    u = gpu_transform(plan, x, y, a)
+    ref = oracle.recurrence(x, y, a, delta, tau, W)
+    assert rel_inf(u, ref, a) <= {"fp64": TOL_ARITH64, "fp32": 5e-6}[prec]

@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # multiply-add of the recurrence (4) and the evaluation at targets (2 per target, half
 # of the points); plus 2 per point (difference and scaling of the gap).
 C_CE = 8
-KERNELS_PER_TRANSFORM = 12   # histogram, pass plan, 8 radix passes, forward and backward sweeps
+KERNELS_PER_TRANSFORM = 15   # item table, histogram, pass plan, pass chain, 8 radix passes, merge, two sweeps
 WORKLOAD = ("plain FP64 at scale: M=N=2^26, x,y ~ U[0,1), alpha ~ N(0,1), delta=%g, eps=%g, unsorted "
             "inputs (sort timed), seed 0")
 

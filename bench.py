@@ -494,6 +494,15 @@ def identical_points(X, A, dev, world, stream):
                      "exact_self_ms": ms_ex})
         del ws
         torch.cuda.empty_cache()
+    # the FP32 sweeps on the same points
+    p32 = fgt.Plan(1.0, 1e-6, precision="fp32")
+    ws = fgt.Workspace(dev)
+    ms32 = _event_time(lambda: fgt.transform_self(p32, X, A_, out=U, workspace=ws, sync_check=False), 3, 3, stream)
+    fgt.transform_self(p32, X, A_, out=U, workspace=ws)
+    out.append({"points": "uniform", "precision": "fp32", "eps": 1e-6, "n_e": p32.n_e,
+                "points_per_s": world * N / (ms32 * 1e-3), "ms": ms32})
+    del ws
+    torch.cuda.empty_cache()
     # Sec. 5's second point set: Chebyshev points on [0, 1]
     from paper_1909_09825_gb300 import inputs
     xc, _ = inputs.chebyshev(N, seed=0)

@@ -161,7 +161,7 @@ int fgt1d_execute_batched(fgt1d_plan plan, int B, const int64_t* x_off, const in
  * and the backward state exclusive, so the self term and every coincident pair get
  * S_n(0) as in Fig. 4.1; with FGT1D_EXACT_SELF they get G(0) = 1 (each u_i gains
  * (1 - S_n(0)) times the total strength of the points at exactly x_i, itself included).
- * Workspace: fgt1d_self_workspace_size.  FP64 plans (FP32 and F32X2 plans return
+ * Workspace: fgt1d_self_workspace_size.  FP64 and FP32 plans (F32X2 plans return
  * FGT1D_EUNSUPPORTED).  N = 0 is a no-op.  Errors as fgt1d_execute. */
 int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes);
 int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,

@@ -536,7 +536,7 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
 // ---- identical targets and sources --------------------------------------------------------
 extern "C" int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* bytes) {
     if (!plan || !bytes || !sizes_ok(0, N)) return FGT1D_EINVAL;
-    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) return FGT1D_EUNSUPPORTED;
+    if (plan->flags & FGT1D_F32X2) return FGT1D_EUNSUPPORTED;
     *bytes = make_layout(0, N, 1, plan->n_e, plan->flags, true, false).total;
     return FGT1D_OK;
 }
@@ -544,7 +544,7 @@ extern "C" int fgt1d_self_workspace_size(fgt1d_plan plan, int64_t N, size_t* byt
 extern "C" int fgt1d_execute_self(fgt1d_plan plan, const double* x, int64_t N, const double* alpha, double* u,
                                   void* workspace, size_t ws_bytes, fgt1d_stream stream) {
     if (!plan || !sizes_ok(0, N)) return FGT1D_EINVAL;
-    if (plan->flags & (FGT1D_FP32 | FGT1D_F32X2)) return FGT1D_EUNSUPPORTED;
+    if (plan->flags & FGT1D_F32X2) return FGT1D_EUNSUPPORTED;
     if (N == 0) return FGT1D_OK;
     if (!x || !alpha || !u) return FGT1D_EINVAL;
     Layout L = make_layout(0, N, 1, plan->n_e, plan->flags, true, false);

@@ -129,7 +129,7 @@ struct SweepArgs {
     uint32_t* tile_ctr;     // [2]
     uint32_t* status;
     int reuse = 0;          // 1: the multiplier table holds a bound geometry's multipliers
-    int self = 0;           // 1: identical targets and sources (every point is both; FP64)
+    int self = 0;           // 1: identical targets and sources (every point is both; FP64, FP32)
 };
 
 // Evaluation channels of the sweeps: bit 0 values Re sum W (h+ + h-) into u, bit 1 the

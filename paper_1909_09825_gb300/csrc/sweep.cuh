@@ -975,11 +975,21 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
     Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    // identical points on the FP32 path: every slot keeps its strength, so the value
+    // channel accumulates over the second half of the coordinate region instead (free:
+    // the gaps take the first half and the derivative channel is off in this mode)
+    const bool self_acc = std::is_same<Real, float>::value && a.self != 0;
+    if (self_acc) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = Real(0);
+    }
+    Real* s_val = self_acc ? s_acc2 : s_al;  // where the value channel accumulates
+    const uint32_t zmask = self_acc ? 0u : tmask;  // slots that hold no strength
     // strength of point r in phase A: a target slot holds a running value once an earlier
     // group's phase C has passed (recomputed-multiplier paths)
     auto strength = [&](int r) {
         if constexpr (!kF64) {
-            if ((tmask >> r) & 1u) return Real(0);
+            if ((zmask >> r) & 1u) return Real(0);
         }
         return s_al[pad<R>(i0 + r)];
     };
@@ -1113,22 +1123,40 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 // recomputed multipliers: the value channel accumulates in the targets' own
                 // (zero) strength slots, so the loop needs no register array and is only
                 // partly unrolled (smaller code per Taylor degree)
-                with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
+                // (identical points: every slot keeps its strength and the values go to
+                // s_acc2; a compile-time variant, so the usual loop is unchanged)
+                auto run_c = [&](auto Self) {
+                    constexpr bool kSelf = decltype(Self)::value;
+                    with_degree<Real>(taylor_degree<Real>(c, k, hw), [&](auto Dc) {
 #pragma unroll kUnrollC
-                    for (int r = 0; r < R; ++r) {
-                        Real mr, mi;
-                        taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
-                        const bool tg = (tmask >> r) & 1u;
-                        Real* slot = &s_al[pad<R>(i0 + r)];
-                        const Real v = *slot;  // strength at a source, running value at a target
-                        cfma_ra<Real>(mr, mi, fr, fi, tg ? Real(0) : v, fr, fi);
-                        if (tg) {
-                            if constexpr ((EV & 1) != 0) *slot = fma(Wr, fr, fma(-Wi, fi, v));
-                            if constexpr ((EV & 2) != 0)
-                                s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+                        for (int r = 0; r < R; ++r) {
+                            Real mr, mi;
+                            taylor<Real>(c, k, Dc, s_th[pad<R>(i0 + r)], mr, mi);
+                            const bool tg = (tmask >> r) & 1u;
+                            Real* slot = &s_al[pad<R>(i0 + r)];
+                            const Real v = *slot;  // strength at a source, running value at a target
+                            cfma_ra<Real>(mr, mi, fr, fi, tg && !kSelf ? Real(0) : v, fr, fi);
+                            if (tg) {
+                                if constexpr ((EV & 1) != 0) {
+                                    if constexpr (kSelf) {
+                                        Real* vs = &s_acc2[pad<R>(i0 + r)];
+                                        *vs = fma(Wr, fr, fma(-Wi, fi, *vs));
+                                    } else {
+                                        *slot = fma(Wr, fr, fma(-Wi, fi, v));
+                                    }
+                                }
+                                if constexpr ((EV & 2) != 0)
+                                    s_acc2[pad<R>(i0 + r)] = fma(Vr, fr, fma(-Vi, fi, s_acc2[pad<R>(i0 + r)]));
+                            }
                         }
-                    }
-                });
+                    });
+                };
+                if constexpr (std::is_same<Real, float>::value) {
+                    if (self_acc) run_c(std::true_type{});
+                    else run_c(std::false_type{});
+                } else {
+                    run_c(std::false_type{});
+                }
             }
         }
     }
@@ -1146,7 +1174,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 a.u[a.self ? base + i : (int64_t)vals[base + i] - a.N] = real_to_f64<Real>(s_al[pad<R>(i)]);
     } else {
         for (int i = tid; i < nvalid; i += T) {
-            if constexpr ((EV & 1) != 0) static_cast<Real*>(a.fwd)[base + i] = s_al[pad<R>(i)];
+            if constexpr ((EV & 1) != 0) static_cast<Real*>(a.fwd)[base + i] = s_val[pad<R>(i)];
             if constexpr ((EV & 2) != 0) static_cast<Real*>(a.fwd2)[base + i] = s_acc2[pad<R>(i)];
         }
     }
@@ -1265,11 +1293,21 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
     Real* s_acc2 = sizeof(Real) == 8 ? reinterpret_cast<Real*>(s_z) : reinterpret_cast<Real*>(s_z) + SM::TP;
+    // identical points on the FP32 path: every slot keeps its strength, so the value
+    // channel accumulates over the second half of the coordinate region instead (free:
+    // the gaps take the first half and the derivative channel is off in this mode)
+    const bool self_acc = std::is_same<Real, float>::value && a.self != 0;
+    if (self_acc) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_acc2[pad<R>(i0 + r)] = Real(0);
+    }
+    Real* s_val = self_acc ? s_acc2 : s_al;  // where the value channel accumulates
+    const uint32_t zmask = self_acc ? 0u : tmask;  // slots that hold no strength
     // strength of point r in phase A: a target slot holds a running value once an earlier
     // group's phase C has passed (recomputed-multiplier paths)
     auto strength = [&](int r) {
         if constexpr (!kF64) {
-            if ((tmask >> r) & 1u) return Real(0);
+            if ((zmask >> r) & 1u) return Real(0);
         }
         return s_al[pad<R>(i0 + r)];
     };
@@ -1343,20 +1381,37 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
                         }
                     }
                 } else {
-                    // as in the forward sweep: values accumulate in the targets' strength slots
+                    // as in the forward sweep: values accumulate in the targets' strength
+                    // slots, or in s_acc2 with identical points (FP32)
+                    auto run_c = [&](auto Self) {
+                        constexpr bool kSelf = decltype(Self)::value;
 #pragma unroll kUnrollC
-                    for (int r = R - 1; r >= 0; --r) {
-                        Real mr, mi;
-                        mult_at(k, Dc, r, mr, mi);
-                        const bool tg = (tmask >> r) & 1u;
-                        Real* slot = &s_al[pad<R>(i0 + r)];
-                        const Real v = *slot;
-                        cfma_ra<Real>(mr, mi, br, bi, tg ? Real(0) : v, br, bi);
-                        if (tg) {
-                            if constexpr ((EV & 1) != 0) *slot = fma(Wr, br, fma(-Wi, bi, v));
-                            if constexpr ((EV & 2) != 0)
-                                s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                        for (int r = R - 1; r >= 0; --r) {
+                            Real mr, mi;
+                            mult_at(k, Dc, r, mr, mi);
+                            const bool tg = (tmask >> r) & 1u;
+                            Real* slot = &s_al[pad<R>(i0 + r)];
+                            const Real v = *slot;
+                            cfma_ra<Real>(mr, mi, br, bi, tg && !kSelf ? Real(0) : v, br, bi);
+                            if (tg) {
+                                if constexpr ((EV & 1) != 0) {
+                                    if constexpr (kSelf) {
+                                        Real* vs = &s_acc2[pad<R>(i0 + r)];
+                                        *vs = fma(Wr, br, fma(-Wi, bi, *vs));
+                                    } else {
+                                        *slot = fma(Wr, br, fma(-Wi, bi, v));
+                                    }
+                                }
+                                if constexpr ((EV & 2) != 0)
+                                    s_acc2[pad<R>(i0 + r)] = fma(-Vr, br, fma(Vi, bi, s_acc2[pad<R>(i0 + r)]));
+                            }
                         }
+                    };
+                    if constexpr (std::is_same<Real, float>::value) {
+                        if (self_acc) run_c(std::true_type{});
+                        else run_c(std::false_type{});
+                    } else {
+                        run_c(std::false_type{});
                     }
                 }
             });
@@ -1382,7 +1437,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
             const uint32_t v = vals[p];
             const int64_t t = (int64_t)v - (a.self ? 0 : a.N);
             if constexpr ((EV & 1) != 0) {
-                double ui = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_al[pad<R>(i)]);
+                double ui = real_to_f64<Real>(static_cast<const Real*>(a.fwd)[p] + s_val[pad<R>(i)]);
                 if (a.self) ui -= s0 * __ldg(&a.alpha[v]);
                 a.u[t] = ui;
             }

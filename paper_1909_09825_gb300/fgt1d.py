@@ -278,7 +278,7 @@ def gauss_transform(x, y, alpha, delta, eps=1e-10, precision="fp64"):
 
 def transform_self(plan, x, alpha, out=None, workspace=None, stream=None, sync_check=True):
     """u_i = sum_j exp(-(x_i - x_j)^2 / (4 delta)) alpha_j with the N points as both
-    targets and sources (fgt1d_execute_self: one sort of N points; FP64 plans).  The
+    targets and sources (fgt1d_execute_self: one sort of N points; fp64 and fp32 plans).  The
     self pair and coincident pairs get S_n(0), or G(0) = 1 with an exact_self plan."""
     _dev(x, "x"), _dev(alpha, "alpha")
     N = x.numel()

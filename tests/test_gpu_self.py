@@ -112,9 +112,44 @@ def test_self_exact_vs_direct(cuda):
     assert rel_inf(u[idx], oracle.direct(x[idx], x, a, 1e-4), a) <= 2e-8 + 1e-13
 
 
+TOL_ARITH32 = 5e-6  # the FP32 path's arithmetic budget (eps >= 1e-6)
+
+
+@pytest.mark.parametrize("N", [1, 100, 4097, 30001])
+def test_self_fp32_vs_oracle(cuda, N):
+    """FP32 sweeps with identical points (the value channel accumulates apart from the
+    strengths, which every point keeps)."""
+    x, _, _ = inputs.uniform(N, 1, seed=N + 2)
+    a = np.random.default_rng(N + 3).standard_normal(N)
+    n, tau, W, En = soe_cf.plan_soe(1e-6)
+    for delta in (1.0, 1e-4):
+        plan = fgt.Plan(delta, soe=(tau, W), precision="fp32")
+        u = _self(plan, x, a, cuda)
+        assert rel_inf(u, oracle.recurrence_self(x, a, delta, tau, W), a) <= TOL_ARITH32
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_self_fp32_ties_and_exact(cuda, exact):
+    x, _, a = inputs.with_ties(9000, 9000, seed=24, n_distinct=50)
+    n, tau, W, En = soe_cf.plan_soe(1e-6)
+    plan = fgt.Plan(1e-2, soe=(tau, W), precision="fp32", exact_self=exact)
+    u = _self(plan, x, a, cuda)
+    assert rel_inf(u, oracle.recurrence_self(x, a, 1e-2, tau, W, exact_self=exact), a) <= TOL_ARITH32
+
+
+def test_self_fp32_vs_direct(cuda):
+    """FP32 identical points against the direct Gauss sum at 2 eps + 5e-6 (Chebyshev
+    points, presorted: the sort is one merge)."""
+    x, a = inputs.chebyshev(40000, seed=5)
+    plan = fgt.Plan(1e-3, 1e-6, precision="fp32")
+    u = _self(plan, x, a, cuda)
+    idx = np.arange(0, 40000, 997)
+    assert rel_inf(u[idx], oracle.direct(x[idx], x, a, 1e-3), a) <= 2e-6 + 5e-6
+
+
 def test_self_unsupported_plans(cuda):
     x = torch.rand(100, dtype=torch.float64, device=cuda)
-    for plan in (fgt.Plan(1e-3, 1e-6, precision="fp32"), fgt.Plan(1e-3, 1e-6, precision="f32x2")):
+    for plan in (fgt.Plan(1e-3, 1e-6, precision="f32x2"),):
         with pytest.raises(_lib.FGTError) as e:
             fgt.transform_self(plan, x, x)
         assert e.value.code == _lib.FGT1D_EUNSUPPORTED

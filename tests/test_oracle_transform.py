@@ -126,6 +126,25 @@ def test_sort_matches_numpy_stable_argsort():
     assert np.array_equal(perm, np.argsort(z, kind="stable"))
 
 
+def test_sort_presorted_runs_is_a_merge():
+    """Sources and targets each presorted (ties, signed zeros): the stable merged order
+    is the merge of the two runs with sources first on equal coordinates."""
+    x, y, _ = inputs.with_ties(3000, 2000, seed=5, n_distinct=30)
+    x, y = np.sort(x, kind="stable"), np.sort(y, kind="stable")
+    perm = oracle.sort_merged(x, y)
+    N = len(y)
+    i = j = 0
+    merged = []
+    while i < N or j < len(x):  # two-run merge, written out
+        if i < N and (j == len(x) or y[i] <= x[j]):
+            merged.append(i)
+            i += 1
+        else:
+            merged.append(N + j)
+            j += 1
+    assert np.array_equal(perm, np.array(merged))
+
+
 def test_sort_rejects_nonfinite():
     with pytest.raises(ValueError):
         oracle.sort_merged(np.array([0.1, np.nan]), np.array([0.2]))

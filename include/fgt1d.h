@@ -88,7 +88,9 @@ int fgt1d_soe_cf(int n, int* n_e, double* tau_re, double* tau_im, double* w_re, 
 /* Plan for bandwidth delta and accuracy eps: picks the smallest even n with
  * E_n <= eps (Sec. 3.3), keeps half of the conjugate pairs (Sec. 4) and
  * precomputes the per-term constants.  flags: FGT1D_FP64, FGT1D_FP32 or FGT1D_F32X2,
- * optionally or-ed with FGT1D_EXACT_SELF (fgt1d_execute only).
+ * optionally or-ed with FGT1D_EXACT_SELF (honoured by fgt1d_execute, fgt1d_execute_host,
+ * fgt1d_execute_noalloc, fgt1d_execute_self and fgt1d_geometry_apply; the batched
+ * transform and fgt1d_backward ignore it).
  * Errors: FGT1D_EINVAL (delta <= 0/non-finite, eps not in (0, 0.5), unknown flags or
  * both FP32 and F32X2, out == NULL), FGT1D_EUNSUPPORTED (eps < E_n of FGT1D_MAX_N, or
  * FP32 with eps < 1e-6), FGT1D_ENOMEM. */
@@ -252,7 +254,10 @@ int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y,
 
 /* Steps a1-a2 alone (Sec. 4, first step; Sec. 5 sorting): the stable sort of the
  * merged points.  perm[p] (device, uint32, length M + N) receives the merged index at
- * sorted position p.  Workspace from fgt1d_sort_workspace_size. */
+ * sorted position p.  Workspace from fgt1d_sort_workspace_size.  Like every entry point
+ * that sorts, it detects sources and targets that each arrive in non-decreasing order
+ * (Sec. 5's pre-sorted points) and then merges the two runs in one pass instead of
+ * running the radix passes; the permutation is the same either way. */
 int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes);
 int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,
                       void* workspace, size_t ws_bytes, fgt1d_stream stream);

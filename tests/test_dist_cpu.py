@@ -47,3 +47,25 @@ def test_max_over_ranks_gloo():
 def test_max_over_ranks_single_process():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def _run_reference(rank, world):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", str(world),
+                          "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_rank0_prints_one_line_others_exit():
+    """bench.py --impl reference under a two-rank launch: rank 0 times the oracle on the
+    host and prints one JSON line; rank 1 exits 0 without work."""
+    (line,) = _run_reference(0, 2)
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "points/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert _run_reference(1, 2) == []

@@ -226,11 +226,14 @@ int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* 
  * counterpart in the paper).  Takes only the inputs and the output: its scratch is a
  * fixed 16 MiB array in the library's device memory, held on every GPU that loads the
  * library until the process exits, which fits any plan with M + N <= 65,536 points;
- * more points return FGT1D_ETOOLARGE.  The first call on a device looks up the
- * array's address (once per device, that device current): make it before any stream
- * capture.  All calls share the array, so calls whose GPU work can overlap race and
- * must be ordered by the caller.  Device-side conditions (NaN/Inf coordinates, an
- * expired wait) are not reported by this entry point. */
+ * more points return FGT1D_ETOOLARGE.  Pointer rules and errors as fgt1d_execute
+ * (a NULL array with a nonzero size returns FGT1D_EINVAL before any GPU work).  The
+ * first call on a device with M > 0 and N > 0 looks up the array's address (once per
+ * device, that device current; a failed lookup returns FGT1D_ECUDA and is retried by
+ * the next call): make it before any stream capture.  All calls share the array, so
+ * calls whose GPU work can overlap race and must be ordered by the caller.
+ * Device-side conditions (NaN/Inf coordinates, an expired wait) are not reported by
+ * this entry point. */
 int fgt1d_execute_noalloc(fgt1d_plan plan, const double* x, int64_t M, const double* y,
                           const double* alpha, int64_t N, double* u, fgt1d_stream stream);
 

@@ -15,6 +15,8 @@
  *                  recurrence eq. 4.5 and backward recurrence eq. 4.6 with the
  *                  exponentials of consecutive gaps, evaluation eq. 4.1 and
  *                  unpermutation.
+ *   o3_recurrence_par / o3_sort_merged_par  the same algorithm and sort on several
+ *                  host cores (coordinate segments with directly computed span carries).
  *   o1_grad / o2_grad  direct O(MN) gradients of L = sum_i g_i u_i with respect to
  *                  alpha, x, y and delta, for the Gaussian and for the SOE kernel.
  */
@@ -295,6 +297,253 @@ int o3_recurrence_self(const double* x, const double* alpha, int64_t N, double d
         u[perm[i]] = acc;
     }
     free(perm); free(hre); free(him);
+    return 0;
+}
+
+/* ---- O3 on several host cores -----------------------------------------------------------
+ * The same algorithm split over coordinate segments, for the multi-core CPU baseline and
+ * for checking the GPU element by element at full size in seconds.
+ *
+ * Sort: the merged points as (coordinate, merged index) records; T contiguous chunks of
+ * the merged order are sorted in parallel by a stable merge sort, then adjacent sorted
+ * runs are merged pairwise (left run first on equal coordinates), so the order is the
+ * stable one of o3_sort_merged, bit for bit.
+ *
+ * Recurrences: eqs. 4.5-4.6 are affine in the state, so a segment [b, e) of the sorted
+ * points can be swept with zero state entering it and corrected afterwards.  Pass 1
+ * (parallel over segments) gives each segment's forward aggregate at its last point and
+ * its backward aggregate at its first point (that point's own strength included).
+ * The carries are then composed in order, each step multiplying by the exponential of a
+ * span computed directly from two FP64 coordinates (no product over points).  Pass 2
+ * (parallel over segments) sweeps each segment again from its true entering state,
+ * as o3_recurrence does, and evaluates eq. 4.1 at its targets. */
+
+typedef struct {
+    double z;
+    int64_t q;
+} zrec_t;
+
+/* stable merge of sorted runs a[0, na) and b[0, nb) into out: a first on ties */
+static void merge_runs(const zrec_t* a, int64_t na, const zrec_t* b, int64_t nb, zrec_t* out) {
+    int64_t i = 0, j = 0, k = 0;
+    while (i < na && j < nb) {
+        if (b[j].z < a[i].z) out[k++] = b[j++];
+        else out[k++] = a[i++];
+    }
+    while (i < na) out[k++] = a[i++];
+    while (j < nb) out[k++] = b[j++];
+}
+
+static void merge_sort_rec(zrec_t* a, zrec_t* tmp, int64_t n) {
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            merge_runs(a + lo, mid - lo, a + mid, hi - mid, tmp + lo);
+        }
+        memcpy(a, tmp, (size_t)n * sizeof(zrec_t));
+    }
+}
+
+/* Sorted records of the merged points with nthreads threads (0: OpenMP default).
+ * Returns 0, -1 for a NaN or infinite coordinate, -2 on allocation failure. */
+static int sort_records_par(const double* x, int64_t M, const double* y, int64_t N, zrec_t* r, int nthreads) {
+    const int64_t P = M + N;
+    int bad = 0;
+    for (int64_t q = 0; q < P; ++q) {
+        r[q].z = q < N ? y[q] : x[q - N];
+        r[q].q = q;
+        if (!isfinite(r[q].z)) bad = 1;
+    }
+    if (bad) return -1;
+    if (P < 2) return 0;
+    zrec_t* tmp = (zrec_t*)malloc((size_t)P * sizeof(zrec_t));
+    if (!tmp) return -2;
+    int T = 1;
+#ifdef _OPENMP
+    T = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    int64_t nch = 1;
+    while (nch < T && nch * 2 <= P) nch *= 2; /* a power of two, for the pairwise rounds */
+    const int64_t len = (P + nch - 1) / nch;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(T)
+#endif
+    for (int64_t c = 0; c < nch; ++c) {
+        int64_t lo = c * len, hi = lo + len < P ? lo + len : P;
+        if (lo < hi) merge_sort_rec(r + lo, tmp + lo, hi - lo);
+    }
+    zrec_t *src = r, *dst = tmp;
+    for (int64_t w = len; w < P; w *= 2) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(T)
+#endif
+        for (int64_t lo = 0; lo < P; lo += 2 * w) {
+            int64_t mid = lo + w < P ? lo + w : P;
+            int64_t hi = lo + 2 * w < P ? lo + 2 * w : P;
+            merge_runs(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
+        }
+        zrec_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != r) memcpy(r, src, (size_t)P * sizeof(zrec_t));
+    free(tmp);
+    return 0;
+}
+
+/* The stable merged order of o3_sort_merged, computed on several threads. */
+int o3_sort_merged_par(const double* x, int64_t M, const double* y, int64_t N, int64_t* perm, int nthreads) {
+    const int64_t P = M + N;
+    zrec_t* r = (zrec_t*)malloc((size_t)(P > 0 ? P : 1) * sizeof(zrec_t));
+    if (!r) return -2;
+    int rc = sort_records_par(x, M, y, N, r, nthreads);
+    if (rc == 0)
+        for (int64_t p = 0; p < P; ++p) perm[p] = r[p].q;
+    free(r);
+    return rc;
+}
+
+/* e^{-tau_k d / sqrt(delta)} for a coordinate distance d >= 0 */
+static inline void decay(double tre, double tim, double d, double sd, double* er, double* ei) {
+    double mag = exp(-tre * d / sd), ang = tim * d / sd;
+    *er = mag * cos(ang);
+    *ei = -mag * sin(ang);
+}
+
+/* O3 over nseg coordinate segments on nthreads threads (0: OpenMP default); exact_self
+ * as in o3_recurrence.  perm_out (may be NULL) receives the sorted merged order.
+ * Returns 0, or -1 (NaN/Inf coordinate), -2 (allocation), -3 (bad n_e). */
+int o3_recurrence_par(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                      double delta, int n_e, const double* tre, const double* tim, const double* wre,
+                      const double* wim, int exact_self, int nseg, int nthreads, double* u, int64_t* perm_out) {
+    const int64_t P = M + N;
+    if (n_e < 1 || n_e > ORACLE_MAX_TERMS) return -3;
+    if (M == 0) return 0;
+    if (nseg < 1) nseg = 1;
+    if (nseg > P) nseg = (int)P;
+    int T = 1;
+#ifdef _OPENMP
+    T = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    zrec_t* r = (zrec_t*)malloc((size_t)P * sizeof(zrec_t));
+    /* per segment: forward aggregate (last point) and backward aggregate (first point),
+     * then the composed carries */
+    double* agg = (double*)calloc((size_t)nseg * n_e * 4, sizeof(double));
+    double* car = (double*)calloc((size_t)nseg * n_e * 4, sizeof(double));
+    if (!r || !agg || !car) { free(r); free(agg); free(car); return -2; }
+    int rc = sort_records_par(x, M, y, N, r, nthreads);
+    if (rc) { free(r); free(agg); free(car); return rc; }
+    if (perm_out)
+        for (int64_t p = 0; p < P; ++p) perm_out[p] = r[p].q;
+    const double sd = sqrt(delta);
+    double s0 = 0.0;
+    for (int k = 0; k < n_e; ++k) s0 += wre[k];
+#define SEG_LO(g) ((int64_t)(((__int128)P * (g)) / nseg))
+    /* pass 1: aggregates with zero entering state */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(T)
+#endif
+    for (int g = 0; g < nseg; ++g) {
+        const int64_t b = SEG_LO(g), e = SEG_LO(g + 1);
+        for (int k = 0; k < n_e; ++k) {
+            double Fr = 0.0, Fi = 0.0, Br = 0.0, Bi = 0.0, er, ei, t;
+            for (int64_t p = b; p < e; ++p) {
+                if (p > b) {
+                    decay(tre[k], tim[k], r[p].z - r[p - 1].z, sd, &er, &ei);
+                    t = er * Fr - ei * Fi; Fi = er * Fi + ei * Fr; Fr = t;
+                }
+                if (r[p].q < N) Fr += alpha[r[p].q];
+            }
+            for (int64_t p = e - 1; p >= b; --p) {
+                if (p < e - 1) {
+                    decay(tre[k], tim[k], r[p + 1].z - r[p].z, sd, &er, &ei);
+                    t = er * Br - ei * Bi; Bi = er * Bi + ei * Br; Br = t;
+                }
+                if (r[p].q < N) Br += alpha[r[p].q]; /* inclusive of the first point */
+            }
+            double* a = agg + ((size_t)g * n_e + k) * 4;
+            a[0] = Fr; a[1] = Fi; a[2] = Br; a[3] = Bi;
+        }
+    }
+    /* carries: car[g] = forward state at the last point of segment g - 1 and the
+     * (inclusive) backward state at the first point of segment g + 1, each composed
+     * from the aggregates with direct span exponentials */
+    for (int k = 0; k < n_e; ++k) {
+        double Fr = 0.0, Fi = 0.0, er, ei, t;
+        for (int g = 0; g < nseg; ++g) {
+            double* c = car + ((size_t)g * n_e + k) * 4;
+            c[0] = Fr; c[1] = Fi;
+            const double* a = agg + ((size_t)g * n_e + k) * 4;
+            if (g > 0) {
+                decay(tre[k], tim[k], r[SEG_LO(g + 1) - 1].z - r[SEG_LO(g) - 1].z, sd, &er, &ei);
+                t = er * Fr - ei * Fi; Fi = er * Fi + ei * Fr; Fr = t;
+            }
+            Fr += a[0]; Fi += a[1];
+        }
+        double Br = 0.0, Bi = 0.0;
+        for (int g = nseg - 1; g >= 0; --g) {
+            double* c = car + ((size_t)g * n_e + k) * 4;
+            c[2] = Br; c[3] = Bi;
+            const double* a = agg + ((size_t)g * n_e + k) * 4;
+            if (g < nseg - 1) {
+                decay(tre[k], tim[k], r[SEG_LO(g + 1)].z - r[SEG_LO(g)].z, sd, &er, &ei);
+                t = er * Br - ei * Bi; Bi = er * Bi + ei * Br; Br = t;
+            }
+            Br += a[2]; Bi += a[3];
+        }
+    }
+    /* pass 2: each segment from its true entering states; evaluation at targets */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(T)
+#endif
+    for (int g = 0; g < nseg; ++g) {
+        const int64_t b = SEG_LO(g), e = SEG_LO(g + 1);
+        for (int64_t p = b; p < e; ++p)
+            if (r[p].q >= N) u[r[p].q - N] = 0.0;
+        for (int k = 0; k < n_e; ++k) {
+            const double* c = car + ((size_t)g * n_e + k) * 4;
+            double Fr = c[0], Fi = c[1], er, ei, t;
+            for (int64_t p = b; p < e; ++p) {
+                if (p > 0) {
+                    decay(tre[k], tim[k], r[p].z - r[p - 1].z, sd, &er, &ei);
+                    t = er * Fr - ei * Fi; Fi = er * Fi + ei * Fr; Fr = t;
+                }
+                if (r[p].q < N) Fr += alpha[r[p].q];
+                else u[r[p].q - N] += wre[k] * Fr - wim[k] * Fi;
+            }
+            /* backward: h-_p = e^{-t (z_{p+1} - z_p)} (h-_{p+1} + alpha_{p+1} [source]);
+             * entering the segment's last point from the next segment's inclusive state */
+            double Br = 0.0, Bi = 0.0;
+            if (e < P) {
+                decay(tre[k], tim[k], r[e].z - r[e - 1].z, sd, &er, &ei);
+                Br = er * c[2] - ei * c[3];
+                Bi = er * c[3] + ei * c[2];
+            }
+            for (int64_t p = e - 1; p >= b; --p) {
+                if (r[p].q >= N) u[r[p].q - N] += wre[k] * Br - wim[k] * Bi;
+                if (p > b) {
+                    double cr = Br + (r[p].q < N ? alpha[r[p].q] : 0.0), ci = Bi;
+                    decay(tre[k], tim[k], r[p].z - r[p - 1].z, sd, &er, &ei);
+                    Br = er * cr - ei * ci;
+                    Bi = er * ci + ei * cr;
+                }
+            }
+        }
+        if (exact_self) {
+            /* sources that share a target's coordinate sit just before it (stable order);
+             * the run may start in an earlier segment */
+            for (int64_t p = b; p < e; ++p) {
+                if (r[p].q < N) continue;
+                double same = 0.0;
+                for (int64_t q = p - 1; q >= 0 && r[q].z == r[p].z; --q)
+                    if (r[q].q < N) same += alpha[r[q].q];
+                u[r[p].q - N] += (1.0 - s0) * same;
+            }
+        }
+    }
+#undef SEG_LO
+    free(r); free(agg); free(car);
     return 0;
 }
 

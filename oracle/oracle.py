@@ -42,6 +42,10 @@ def lib():
         L.o3_recurrence_self.restype = i32
         L.o3_sort_merged.argtypes = [p, i64, p, i64, p]
         L.o3_sort_merged.restype = i32
+        L.o3_sort_merged_par.argtypes = [p, i64, p, i64, p, i32]
+        L.o3_sort_merged_par.restype = i32
+        L.o3_recurrence_par.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, i32, i32, i32, p, p]
+        L.o3_recurrence_par.restype = i32
         L.o1_grad.argtypes = [p, i64, p, p, i64, d, p, p, p, p, p]
         L.o2_grad.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, p, p, p, p, p]
         L.oracle_openmp_max_threads.restype = i32
@@ -110,6 +114,34 @@ def recurrence_self(x, alpha, delta, tau, W, exact_self=False):
     if rc != 0:
         raise ValueError("oracle self recurrence failed: %d" % rc)
     return u
+
+
+def recurrence_par(x, y, alpha, delta, tau, W, exact_self=False, nseg=None, nthreads=0, return_perm=False):
+    """O3 on several host cores: the same sort and recurrences over nseg coordinate
+    segments (default 8 per thread), carries composed with direct span exponentials."""
+    x, y, alpha = _f64(x), _f64(y), _f64(alpha)
+    n, tr, ti, wr, wi = _soe(tau, W)
+    threads = nthreads if nthreads > 0 else max_threads()
+    if nseg is None:
+        nseg = 8 * threads
+    u = np.empty(len(x))
+    perm = np.empty(len(x) + len(y), dtype=np.int64) if return_perm else None
+    rc = lib().o3_recurrence_par(_ptr(x), len(x), _ptr(y), _ptr(alpha), len(y), float(delta), n,
+                                 _ptr(tr), _ptr(ti), _ptr(wr), _ptr(wi), int(bool(exact_self)), int(nseg),
+                                 int(nthreads), _ptr(u), _ptr(perm) if return_perm else None)
+    if rc != 0:
+        raise ValueError("oracle parallel recurrence failed: %d" % rc)
+    return (u, perm) if return_perm else u
+
+
+def sort_merged_par(x, y, nthreads=0):
+    """sort_merged on several threads (the same stable order, bit for bit)."""
+    x, y = _f64(x), _f64(y)
+    perm = np.empty(len(x) + len(y), dtype=np.int64)
+    rc = lib().o3_sort_merged_par(_ptr(x), len(x), _ptr(y), len(y), _ptr(perm), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle parallel sort failed: %d" % rc)
+    return perm
 
 
 def sort_merged(x, y):

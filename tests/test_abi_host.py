@@ -176,3 +176,21 @@ def test_product_imports_no_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle|#include.*oracle|liboracle", txt, re.M), f
+
+
+def test_noalloc_rejects_null_arrays_before_the_gpu(L):
+    """The no-allocation entry point applies fgt1d_execute's pointer rules on the host:
+    a NULL array with a nonzero size is FGT1D_EINVAL, returned before any CUDA call
+    (this container has no GPU, so reaching the device would give FGT1D_ECUDA)."""
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    p = fgt.Plan(1e-3, 1e-6)
+    v = (ctypes.c_double * 8)()
+    f = L.fgt1d_execute_noalloc
+    assert f(p.handle, None, 8, v, v, 8, v, None) == _lib.FGT1D_EINVAL     # x
+    assert f(p.handle, v, 8, v, v, 8, None, None) == _lib.FGT1D_EINVAL     # u
+    assert f(p.handle, v, 8, None, v, 8, v, None) == _lib.FGT1D_EINVAL     # y
+    assert f(p.handle, v, 8, v, None, 8, v, None) == _lib.FGT1D_EINVAL     # alpha
+    assert f(None, v, 8, v, v, 8, v, None) == _lib.FGT1D_EINVAL            # plan
+    assert f(p.handle, v, 40000, v, v, 30000, v, None) == _lib.FGT1D_ETOOLARGE
+    assert f(p.handle, None, 0, None, None, 0, None, None) == _lib.FGT1D_OK  # nothing to do

@@ -1,37 +1,91 @@
-"""Parity at the benchmark's full size (M = N = 2^26, the launch configuration that
-bench.py times): sampled targets checked one by one against the oracle's direct sum
-over all 2^26 sources."""
+"""Parity at the benchmark's full size: M = N = 2^26 uniform points (P = 2^27 merged),
+alpha ~ N(0, 1), seed 0, in the launch configuration bench.py times (default tile).
+
+* every target of the GPU result against the oracle's run of the paper's algorithm
+  (sort, eqs. 4.5-4.6 recurrences, eq. 4.1; the multi-core variant, pinned to the
+  single-thread one), element by element, for delta in {1e-2, 1e-5} and eps in
+  {1e-6, 1e-10} (FP64) and eps = 1e-6 (FP32);
+* 1000 sampled targets against the direct Gauss sum over all 2^26 sources (eq. 1.1),
+  within 2 eps + 1e-13 (FP64), and the oracle's own recurrence error at those targets;
+* the sorted merged order of all 2^27 points, bit for bit, against the oracle's stable
+  sort.
+
+Tolerances: FP64 within 1e-12 sum|alpha| of the oracle's recurrence (both are the same
+SOE operator; what differs is rounding order: chunked scans with directly computed span
+multipliers on the GPU, a sequential product of per-gap exponentials on the CPU); FP32
+within 5e-6 sum|alpha| (the FP32 bulk recurrence's rounding; the benchmark spec's FP32 bar)."""
 import numpy as np
 import pytest
 import torch
 
 import paper_1909_09825_gb300 as fgt
-from oracle import oracle
+from oracle import oracle, soe_cf
 from paper_1909_09825_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
 M = N = 1 << 26
+_o3_cache = {}
 
 
 @pytest.fixture(scope="module")
 def data(cuda):
     x, y, a = inputs.uniform(M, N, seed=0)
-    dev = cuda
-    return x, y, a, torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev), torch.from_numpy(a).to(dev)
+    return x, y, a, torch.from_numpy(x).to(cuda), torch.from_numpy(y).to(cuda), torch.from_numpy(a).to(cuda)
+
+
+def _o3(x, y, a, delta, eps):
+    """The oracle's recurrence on the oracle's own SOE nodes (numpy CF, smallest n with
+    E_n <= eps), cached per (delta, eps)."""
+    key = (delta, eps)
+    if key not in _o3_cache:
+        _, tau, W, _ = soe_cf.plan_soe(eps)
+        _o3_cache[key] = oracle.recurrence_par(x, y, a, delta, tau, W)
+    return _o3_cache[key]
 
 
 @pytest.mark.parametrize("delta,eps,prec", [(1e-5, 1e-6, "fp64"), (1e-5, 1e-10, "fp64"), (1e-2, 1e-6, "fp64"),
-                                            (1e-5, 1e-6, "fp32"), (1e-5, 1e-10, "f32x2")])
-def test_fullsize_sampled(data, delta, eps, prec):
+                                            (1e-2, 1e-10, "fp64"), (1e-5, 1e-6, "fp32"), (1e-2, 1e-6, "fp32")])
+def test_fullsize_every_target_vs_recurrence(data, delta, eps, prec):
+    """Both sides run the oracle's nodes (the GPU plan is built from them), so the
+    comparison isolates the transform from the SOE generator."""
     x, y, a, X, Y, A = data
-    plan = fgt.Plan(delta, eps, precision=prec)
-    u = fgt.transform(plan, X, Y, A)
-    rng = np.random.default_rng(17)
-    idx = np.concatenate([[0, M - 1, int(np.argmin(x)), int(np.argmax(x))], rng.choice(M, 12, replace=False)])
-    ug = u[torch.from_numpy(idx).to(u.device)].cpu().numpy()
-    ref = oracle.direct(x[idx], y, a, delta, nthreads=0)
-    tol = 2 * eps + (5e-6 if prec == "fp32" else 1e-13)
-    assert np.max(np.abs(ug - ref)) / np.abs(a).sum() <= tol
+    _, tau, W, _ = soe_cf.plan_soe(eps)
+    plan = fgt.Plan(delta, soe=(tau, W), precision=prec)
+    ref = _o3(x, y, a, delta, eps)
+    u = fgt.transform(plan, X, Y, A).cpu().numpy()
+    s = np.abs(a).sum()
+    err = np.max(np.abs(u - ref)) / s
+    tol = 5e-6 if prec == "fp32" else 1e-12
+    assert err <= tol, (err, tol)
+    assert np.all(np.isfinite(u))
     del u
+    torch.cuda.empty_cache()
+
+
+def test_fullsize_sampled_vs_direct_sum(data):
+    """1000 targets (the four extremes plus 996 at random) against eq. 1.1 summed over
+    every source; the oracle's recurrence at the same targets shows its own error."""
+    x, y, a, X, Y, A = data
+    delta, eps = 1e-5, 1e-6
+    plan = fgt.Plan(delta, eps)
+    u = fgt.transform(plan, X, Y, A).cpu().numpy()
+    rng = np.random.default_rng(17)
+    idx = np.unique(np.concatenate([[0, M - 1, int(np.argmin(x)), int(np.argmax(x))],
+                                    rng.choice(M, 996, replace=False)]))
+    ref = oracle.direct(x[idx], y, a, delta, nthreads=0)
+    s = np.abs(a).sum()
+    assert np.max(np.abs(u[idx] - ref)) / s <= 2 * eps + 1e-13
+    o3 = _o3(x, y, a, delta, eps)
+    # the CPU recurrence on the oracle's nodes meets the same bound at the same targets
+    assert np.max(np.abs(o3[idx] - ref)) / s <= 2 * eps + 1e-13
+
+
+def test_fullsize_permutation_bit_exact(data):
+    x, y, a, X, Y, A = data
+    perm = fgt.sort_merged(X, Y).cpu().numpy()
+    ref = oracle.sort_merged_par(x, y)
+    assert perm.shape == ref.shape == (2 * M,)
+    assert np.array_equal(perm, ref)
+    del perm
     torch.cuda.empty_cache()

@@ -33,8 +33,8 @@ ALSO = [dict(delta=1e-5, eps=1e-10, precision="fp64"), dict(delta=1e-2, eps=1e-6
         dict(delta=1e-2, eps=1e-10, precision="fp64"), dict(delta=1e-5, eps=1e-3, precision="fp64"),
         dict(delta=1e-5, eps=1e-6, precision="fp32"), dict(delta=1e-2, eps=1e-6, precision="fp32"),
         dict(delta=1e-5, eps=1e-6, precision="f32x2"), dict(delta=1e-5, eps=1e-10, precision="f32x2")]
-# FP64 pipe peak: 152 SMs x 2 DFMA/clk/SM (measured by a DFMA throughput probe on this
-# GB300 pool) x 2 flop x 2070 MHz maximum SM clock.
+# FP64 pipe peak when the run's own measurement (fgt1d_measure_peaks) is unavailable:
+# 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Algorithmic FP64 pipe ops of the forward sweep kernel per (merged point, term): the
 # multiplier exp(-tau theta) as a degree-4 Taylor polynomial (C_ce = 8), one complex
@@ -44,6 +44,20 @@ C_CE = 8
 KERNELS_PER_TRANSFORM = 15   # item table, histogram, pass plan, pass chain, 8 radix passes, merge, two sweeps
 WORKLOAD = ("plain FP64 at scale: M=N=2^26, x,y ~ U[0,1), alpha ~ N(0,1), delta=%g, eps=%g, unsorted "
             "inputs (sort timed), seed 0")
+
+
+def measure_peaks():
+    """The pipes' throughput on this GPU (fgt1d_measure_peaks), measured in this run."""
+    from paper_1909_09825_gb300 import _lib
+    o = (ctypes.c_double * 10)()
+    _lib.check(_lib.lib().fgt1d_measure_peaks(o, None), "measure_peaks")
+    v = list(o)
+    return {"fp64_tflops": 2 * v[0] / 1e12, "fp64_fma_per_clk_per_sm": v[1],
+            "fp32_tflops": 2 * v[2] / 1e12, "fp32_fma_per_clk_per_sm": v[3],
+            "sfu_ex2_per_s": v[4], "sfu_ex2_per_clk_per_sm": v[5],
+            "sfu_sin_per_s": v[6], "sfu_sin_per_clk_per_sm": v[7], "sms": int(v[8]), "sm_mhz": v[9],
+            "how": "fgt1d_measure_peaks: 8 independent FMA/ex2/sin chains per thread, 8 x 256 threads per "
+                   "SM, best of two CUDA-event-timed launches; SM clock from clock64 over globaltimer"}
 
 
 def max_over_ranks(value, device=None):
@@ -261,13 +275,16 @@ def main():
             stages["autotune_ms"] = {str(k): v for k, v in tune.items() if k != "chosen"}
         return plan, ms, stages
 
+    peaks = measure_peaks()
+    fp64_peak = peaks["fp64_tflops"]
     gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     with ClockSampler(gpu_uuid) as clk:
         plan, ms, stages = timed(dict(HEAD, precision=args.precision), args.steps, args.warmup, profile=True)
     clocks = clk.summary()
     value = world * P / (ms * 1e-3)
 
-    # roofline of the dominant kernel (forward sweep, FP64 pipe)
+    # roofline of the dominant kernel (forward sweep, FP64 pipe), against the FP64 FMA
+    # rate measured above in this run (burst, the sweep is timed alone per launch)
     n_e = plan.n_e
     fwd_ops = P * n_e * (C_CE + 4 + 2.0 * M / P) + 2 * P
     fwd_s = stages["fwd_sweep_ms"] * 1e-3
@@ -275,11 +292,23 @@ def main():
     roofline = {"bound": "alu", "pipe": "fp64",
                 "kernel": "k_sweep_fwd<double, %d, %d, %d>" % (n_e, plan.tile_threads, 4096 // plan.tile_threads),
                 "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "152 SMs x 2 DFMA/clk/SM (probe) x 2 flop x 2070 MHz",
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "peak_source": "measured in this run (fgt1d_measure_peaks, DFMA chains, %.0f MHz)" % peaks["sm_mhz"],
                 "algorithmic_ops_per_unit": "unit = (merged point, SOE term); C_ce=%d + 4 + 2 M/P FP64 ops, "
                                             "+2 per point" % C_CE,
                 "traffic": None}
+    # the backward sweep (4 + 2 M/P per point and term) and the whole transform
+    # (n_e (C_ce + 20) FP64 ops per point, the survey's count) against the same peak
+    bwd_ops = P * n_e * (4 + 2.0 * M / P)
+    bwd_ach = 2 * bwd_ops / (stages["bwd_sweep_ms"] * 1e-3) / 1e12
+    whole_ach = 2 * P * n_e * (C_CE + 20) / (ms * 1e-3) / 1e12
+    roofline_more = {
+        "bwd_sweep": {"kernel": "k_sweep_bwd<double, %d, %d, %d, 1>" % (n_e, plan.tile_threads,
+                                                                        4096 // plan.tile_threads),
+                      "achieved": bwd_ach, "frac": bwd_ach / fp64_peak, "unit": "TFLOP/s",
+                      "algorithmic_ops_per_unit": "4 + 2 M/P FP64 ops per (merged point, term)"},
+        "whole_transform": {"achieved": whole_ach, "frac": whole_ach / fp64_peak, "unit": "TFLOP/s",
+                            "algorithmic_ops_per_unit": "n_e (C_ce + 20) FP64 ops per merged point"}}
     traffic = _traffic_record(plan)
     if traffic is not None:
         roofline["traffic"] = traffic * P
@@ -308,8 +337,11 @@ def main():
             err2 = None
             if rank == 0 and not args.no_cpu:
                 err2 = sampled_error(p2, X, Y, A, x, y, a, cfg["delta"], dev, n=4)
-            also.append({"precision": cfg["precision"], "delta": cfg["delta"], "eps": cfg["eps"], "n_e": p2.n_e,
-                         "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2, "error": err2})
+            entry = {"precision": cfg["precision"], "delta": cfg["delta"], "eps": cfg["eps"], "n_e": p2.n_e,
+                     "value": world * P / (ms2 * 1e-3), "ms_per_step": ms2, "stages": st2, "error": err2}
+            if cfg["precision"] == "fp32":
+                entry["roofline"] = hbm_roofline_fp32(st2, x, y, M, N)
+            also.append(entry)
 
     # error of the headline result against the oracle's direct sum at sampled targets
     head_err = None
@@ -320,7 +352,7 @@ def main():
 
     extra = {}
     if not args.no_also:
-        extra["geometry_reuse"] = geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args)
+        extra["geometry_reuse"] = geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args, fp64_peak)
         extra["identical_points"] = identical_points(X, A, dev, world, stream)
         extra["presorted"] = presorted(plan, X, Y, A, x, y, a, dev, world, stream, rank == 0 and not args.no_cpu)
         extra["precision_split"] = precision_split(args, dev, world, P)
@@ -341,7 +373,8 @@ def main():
                            "precision": args.precision, "tile_threads": plan.tile_threads, "l2": "inputs (24 B/point, %.1f GB) larger than the 129 MB L2"
                                                        % (24 * P / 2 ** 30 / 1.0),
                            "parallelism": "replicas" if world > 1 else "single"},
-                "stages": stages, "error": head_err, "roofline": roofline, "cpu_baseline": cpu,
+                "stages": stages, "error": head_err, "roofline": roofline, "roofline_more": roofline_more,
+                "peaks": peaks, "cpu_baseline": cpu,
                 "e2e": {"value": world * P / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 8 * (M + 2 * N),
                         "d2h_bytes_per_step": 8 * M},
                 "gpu_launches": KERNELS_PER_TRANSFORM * args.steps, "clocks": clocks, "also": also, **extra}
@@ -351,6 +384,48 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def hbm_peak():
+    """Measured copy bandwidth of this GPU pool (GB/s) and where it comes from."""
+    f = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(f):
+        return float(json.load(open(f))["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def active_sort_passes(x, y):
+    """Digit passes the sort runs on these points: the 8-bit digits of the
+    order-preserving keys that are not the same for every point."""
+    b = np.concatenate([y, x]).view(np.uint64).copy()
+    b[b == np.uint64(0x8000000000000000)] = 0  # -0.0 as +0.0
+    neg = (b >> np.uint64(63)) == 1
+    k = np.where(neg, ~b, b | np.uint64(0x8000000000000000))
+    n = 0
+    for d in range(8):
+        dg = (k >> np.uint64(8 * d)) & np.uint64(255)
+        n += int(np.any(dg != dg[0]))
+    return max(n, 1)
+
+
+def hbm_roofline_fp32(st, x, y, M, N):
+    """HBM roofline of the FP32 path's two stages, which move memory rather than compute:
+    the sort (8 B read per point by the key/histogram pass, 24 B per point per digit pass:
+    key and code read and written) and the two sweeps (forward: key 8, code 4, strength
+    8 N/P, partial sum 4; backward: key 8, code 4, strength 8 N/P, partial sum 4, value
+    8 M/P, code 4 M/P at targets)."""
+    peak, src = hbm_peak()
+    P = M + N
+    passes = active_sort_passes(x, y)
+    sort_b = P * (8 + 24 * passes)
+    sweep_b = P * (8 + 4 + 8 * N / P + 4) + P * (8 + 4 + 8 * N / P + 4 + 12 * M / P)
+    sort_gbs = sort_b / (st["sort_ms"] * 1e-3) / 1e9
+    sweep_gbs = sweep_b / ((st["fwd_sweep_ms"] + st["bwd_sweep_ms"]) * 1e-3) / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
+            "sort": {"achieved": sort_gbs, "frac": sort_gbs / peak, "passes": passes,
+                     "algorithmic_bytes_per_point": 8 + 24 * passes},
+            "sweeps": {"achieved": sweep_gbs, "frac": sweep_gbs / peak,
+                       "algorithmic_bytes_per_point": sweep_b / P}}
 
 
 def _event_time(fn, steps, warmup, stream):
@@ -397,7 +472,7 @@ def every_target_error(precision, X, Y, A, x, y, a, delta, eps):
             "oracle_s": dt}
 
 
-def geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args):
+def geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args, fp64_peak):
     """Headline workload with fixed points (Sec. 5's pre-sorted points and stored
     exponential table): bind once (sort + FP64 multiplier table), then apply to new
     strength vectors (sweeps only), timed with CUDA events on the launching stream."""
@@ -448,8 +523,8 @@ def geometry_reuse(plan, X, Y, A, x, y, a, dev, world, rank, args):
             "bind_ms": bind_ms, "apply_ms": apply_ms, "apply_points_per_s": world * P / (apply_ms * 1e-3),
             "apply_f32x2_ms": apply_df_ms, "apply_fp32_eps1e-6_ms": apply_32_ms,
             "speedup_vs_full_transform": None, "error_vs_direct": err,
-            "apply_roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                               "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "apply_roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak,
+                               "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                                "algorithmic_ops_per_unit": "unit = (merged point, term): 8 + 4 M/P FP64 ops",
                                "table_bytes_per_point": 2 * 16 * n_e}}
 

@@ -72,11 +72,13 @@ typedef void* fgt1d_stream;              /* a cudaStream_t */
                                  path's rounding; gradients use the FP64 path */
 
 #define FGT1D_MAX_TERMS 8     /* largest n_e a plan can hold */
-#define FGT1D_MAX_N 14        /* largest CF order n built in FP64 (Sec. 3.3) */
+#define FGT1D_MAX_N 16        /* largest CF order n (Sec. 3.3; n <= 14 built in FP64, n = 16
+                                 in double-double arithmetic) */
 
 /* Step a0, the SOE generator (Sec. 2.3 eqs. 2.10-2.13, Sec. 3.3; eq. 3.1 for E_n).
  * Builds the CF type (n-1, n) approximation of e^z on (-inf, 0] for even n in
- * [2, FGT1D_MAX_N] in FP64 on the host and converts it with eq. 2.11.
+ * [2, FGT1D_MAX_N] on the host (FP64 up to n = 14; n = 16 in double-double, as the
+ * paper builds its largest orders in extended precision) and converts it with eq. 2.11.
  * Outputs: *n_e = n/2; tau_k = sqrt(z_k) (one of each conjugate pair, Im tau_k > 0,
  * ascending Re tau_k, delta-free) and W_k = 2 w_k in caller host arrays of length
  * >= FGT1D_MAX_TERMS; *E_n = max |G(x;1) - S_n(x;1)| over the sampled grid (x = 0,
@@ -237,6 +239,54 @@ int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* 
 int fgt1d_execute_noalloc(fgt1d_plan plan, const double* x, int64_t M, const double* y,
                           const double* alpha, int64_t N, double* u, fgt1d_stream stream);
 
+/* Range partition of one transform over several devices or processes (no counterpart
+ * in the paper, whose Sec. 6 only remarks that the method parallelises over modes).  The
+ * recurrences of eqs. 4.5-4.6 are affine in the state, so a contiguous range of the
+ * sorted coordinate line -- a "segment", holding every target and source whose
+ * coordinate falls in it -- can be transformed alone and corrected afterwards by the
+ * states entering it from both sides.  Segments are ordered along the line (g = 0 ..
+ * G-1) and must not interleave: every point of segment g lies at or right of every
+ * point of segment g-1 (points with equal coordinates belong to one segment).
+ *
+ * Boundary record of a segment, FGT1D_SEGMENT_DOUBLES(n_e) doubles:
+ *   [0, n_e) Re F_k, [n_e, 2 n_e) Im F_k: F_k = sum over the segment's sources of
+ *            alpha_j exp(-tau_k (z_last - y_j) / sqrt(delta)), the forward state of
+ *            eq. 4.5 at its last point;
+ *   [2 n_e, 4 n_e) Re G_k, Im G_k: G_k = sum over its sources of alpha_j
+ *            exp(-tau_k (y_j - z_first) / sqrt(delta)), the backward state of eq. 4.6 at
+ *            its first point with that point's own strength included;
+ *   [4 n_e] z_first, [4 n_e + 1] z_last: its smallest and largest coordinate (NaN for a
+ *            segment without points).
+ * A carry record has the same size: Re/Im F_in (the forward state at z_prev, the last
+ * point of the segments to the left), Re/Im G_in (the backward state, inclusive, at
+ * z_next, the first point of the segments to the right), z_prev, z_next (NaN: none).
+ *
+ * fgt1d_segment_execute: the transform of the segment's targets x[M] and sources y[N],
+ *   alpha[N] (device) with zero entering states into u[M] (device), and its boundary
+ *   record into `boundary` (device).  Any of M, N may be 0 (a segment without targets
+ *   still reports its sources' states).  Workspace: fgt1d_workspace_size(plan, M, N);
+ *   it keeps the segment's sorted points for fgt1d_segment_apply.
+ * fgt1d_segment_compose: HOST arithmetic on the boundary records of all G segments
+ *   (`boundaries`, host, G records in order): writes segment g's carry record (host).
+ *   Each step across a segment multiplies by exp(-tau_k d / sqrt(delta)) of a span d
+ *   between two FP64 coordinates, computed directly.  FGT1D_EINVAL if the segments are
+ *   not ordered or a record is not finite.
+ * fgt1d_segment_apply: u[i] += Re sum_k W_k (F_in,k exp(-tau_k (x_i - z_prev)/sqrt(delta))
+ *   + G_in,k exp(-tau_k (z_next - x_i)/sqrt(delta))) for every target of the segment,
+ *   with `carry` a DEVICE copy of its carry record, the workspace of the preceding
+ *   fgt1d_segment_execute (same plan and sizes, not used by another call in between),
+ *   and u as written by it.  Terms below 2^-60 of the carry are skipped.
+ * Together: execute on every segment, gather the G boundary records, compose, apply;
+ * u then equals the transform of all points (up to rounding).  Errors as
+ * fgt1d_execute; FP64, FP32 and F32X2 plans (the carries are FP64 in each). */
+#define FGT1D_SEGMENT_DOUBLES(n_e) (4 * (n_e) + 2)
+int fgt1d_segment_execute(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                          const double* alpha, int64_t N, double* u, double* boundary,
+                          void* workspace, size_t ws_bytes, fgt1d_stream stream);
+int fgt1d_segment_compose(fgt1d_plan plan, int G, int g, const double* boundaries, double* carry);
+int fgt1d_segment_apply(fgt1d_plan plan, int64_t M, int64_t N, const double* carry, double* u,
+                        void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
 /* Gradients of L = sum_i grad_u[i] u_i for the transform computed by fgt1d_execute
  * (the SOE operator of eq. 1.3 with the plan's nodes; the paper has no gradients):
  *   grad_alpha[j] = sum_i grad_u[i] S(x_i - y_j)      (the transform with roles swapped)
@@ -264,6 +314,17 @@ int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y,
 int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes);
 int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,
                       void* workspace, size_t ws_bytes, fgt1d_stream stream);
+
+/* Measures the pipes that bound this library's kernels on the current device (no
+ * counterpart in the paper): long independent chains of FP64 FMA, FP32 FMA and the
+ * special-function unit's ex2.approx and sin.approx on every SM, each timed with CUDA
+ * events on `stream` (best of two after a warm-up launch).  out (host, >= 10 doubles):
+ * out[0], out[1] FP64 FMA per second and per SM per clock cycle; out[2], out[3] the same
+ * for FP32 FMA; out[4], out[5] ex2; out[6], out[7] sin; out[8] the number of SMs; out[9]
+ * the SM clock in MHz during the FP64 run (from the cycle counter and the global timer).
+ * One FMA is two floating-point operations.  Allocates a few bytes of device memory and
+ * synchronises the stream.  Errors: FGT1D_EINVAL (out NULL), FGT1D_ECUDA. */
+int fgt1d_measure_peaks(double* out, fgt1d_stream stream);
 
 /* Synchronises `stream`, then returns and clears the device status recorded in the
  * workspace by the previous compute calls: FGT1D_OK, FGT1D_EINVAL (a bad batch item),

@@ -17,6 +17,8 @@
  *                  unpermutation.
  *   o3_recurrence_par / o3_sort_merged_par  the same algorithm and sort on several
  *                  host cores (coordinate segments with directly computed span carries).
+ *   o3_segment_boundary / o3_carry_apply  a segment's boundary states and the entering
+ *                  states' contribution to its targets, as direct sums.
  *   o1_grad / o2_grad  direct O(MN) gradients of L = sum_i g_i u_i with respect to
  *                  alpha, x, y and delta, for the Gaussian and for the SOE kernel.
  */
@@ -545,6 +547,67 @@ int o3_recurrence_par(const double* x, int64_t M, const double* y, const double*
 #undef SEG_LO
     free(r); free(agg); free(car);
     return 0;
+}
+
+/* ---- segments of a range-partitioned transform (plain definitions) ---------------------
+ * A segment holds the targets x[M] and sources y[N] of one coordinate range.  Its
+ * boundary record (4 n_e + 2 doubles): F_k = sum_j alpha_j e^{-t_k (z_last - y_j)/sqrt(delta)}
+ * (real parts, then imaginary parts), G_k = sum_j alpha_j e^{-t_k (y_j - z_first)/sqrt(delta)}
+ * (real, imaginary), z_first, z_last (the smallest and largest coordinate of all its
+ * points; NaN when it has none).  Direct O(N n_e) sums: eqs. 4.3-4.4 at the segment's
+ * ends. */
+void o3_segment_boundary(const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                         double delta, int n_e, const double* tre, const double* tim, double* out) {
+    double zf = NAN, zl = NAN;
+    for (int64_t i = 0; i < M; ++i) {
+        if (isnan(zf) || x[i] < zf) zf = x[i];
+        if (isnan(zl) || x[i] > zl) zl = x[i];
+    }
+    for (int64_t j = 0; j < N; ++j) {
+        if (isnan(zf) || y[j] < zf) zf = y[j];
+        if (isnan(zl) || y[j] > zl) zl = y[j];
+    }
+    const double sd = sqrt(delta);
+    for (int k = 0; k < n_e; ++k) {
+        double Fr = 0.0, Fi = 0.0, Gr = 0.0, Gi = 0.0, er, ei;
+        for (int64_t j = 0; j < N; ++j) {
+            decay(tre[k], tim[k], zl - y[j], sd, &er, &ei);
+            Fr += alpha[j] * er;
+            Fi += alpha[j] * ei;
+            decay(tre[k], tim[k], y[j] - zf, sd, &er, &ei);
+            Gr += alpha[j] * er;
+            Gi += alpha[j] * ei;
+        }
+        out[k] = Fr; out[n_e + k] = Fi; out[2 * n_e + k] = Gr; out[3 * n_e + k] = Gi;
+    }
+    out[4 * n_e] = zf;
+    out[4 * n_e + 1] = zl;
+}
+
+/* u_i += Re sum_k W_k (F_k e^{-t_k (x_i - z_prev)/sqrt(delta)} + G_k e^{-t_k (z_next - x_i)/sqrt(delta)})
+ * for a carry record (F, G, z_prev, z_next; a NaN coordinate means no neighbour):
+ * the states entering the segment, carried to each target by eqs. 4.5-4.6. */
+void o3_carry_apply(const double* x, int64_t M, double delta, int n_e, const double* tre, const double* tim,
+                    const double* wre, const double* wim, const double* carry, double* u) {
+    const double sd = sqrt(delta), zp = carry[4 * n_e], zn = carry[4 * n_e + 1];
+    for (int64_t i = 0; i < M; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < n_e; ++k) {
+            double er, ei, hr = 0.0, hi = 0.0;
+            if (!isnan(zp)) {
+                decay(tre[k], tim[k], x[i] - zp, sd, &er, &ei);
+                hr += er * carry[k] - ei * carry[n_e + k];
+                hi += er * carry[n_e + k] + ei * carry[k];
+            }
+            if (!isnan(zn)) {
+                decay(tre[k], tim[k], zn - x[i], sd, &er, &ei);
+                hr += er * carry[2 * n_e + k] - ei * carry[3 * n_e + k];
+                hi += er * carry[3 * n_e + k] + ei * carry[2 * n_e + k];
+            }
+            acc += wre[k] * hr - wim[k] * hi;
+        }
+        u[i] += acc;
+    }
 }
 
 /* ---- direct gradients ------------------------------------------------------------------

@@ -46,6 +46,8 @@ def lib():
         L.o3_sort_merged_par.restype = i32
         L.o3_recurrence_par.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, i32, i32, i32, p, p]
         L.o3_recurrence_par.restype = i32
+        L.o3_segment_boundary.argtypes = [p, i64, p, p, i64, d, i32, p, p, p]
+        L.o3_carry_apply.argtypes = [p, i64, d, i32, p, p, p, p, p, p]
         L.o1_grad.argtypes = [p, i64, p, p, i64, d, p, p, p, p, p]
         L.o2_grad.argtypes = [p, i64, p, p, i64, d, i32, p, p, p, p, p, p, p, p, p]
         L.oracle_openmp_max_threads.restype = i32
@@ -142,6 +144,28 @@ def sort_merged_par(x, y, nthreads=0):
     if rc != 0:
         raise ValueError("oracle parallel sort failed: %d" % rc)
     return perm
+
+
+def segment_boundary(x, y, alpha, delta, tau, W):
+    """A segment's boundary record (4 n_e + 2 values: Re F, Im F, Re G, Im G, z_first,
+    z_last) by direct sums over its sources."""
+    x, y, alpha = _f64(x), _f64(y), _f64(alpha)
+    n, tr, ti, _, _ = _soe(tau, W)
+    out = np.empty(4 * n + 2)
+    lib().o3_segment_boundary(_ptr(x), len(x), _ptr(y), _ptr(alpha), len(y), float(delta), n, _ptr(tr), _ptr(ti),
+                              _ptr(out))
+    return out
+
+
+def carry_apply(x, u, delta, tau, W, carry):
+    """u + the contribution of a carry record (F_in, G_in, z_prev, z_next) at targets x."""
+    x = _f64(x)
+    n, tr, ti, wr, wi = _soe(tau, W)
+    u = np.array(u, dtype=np.float64, copy=True)
+    carry = _f64(carry)
+    lib().o3_carry_apply(_ptr(x), len(x), float(delta), n, _ptr(tr), _ptr(ti), _ptr(wr), _ptr(wi), _ptr(carry),
+                         _ptr(u))
+    return u
 
 
 def sort_merged(x, y):

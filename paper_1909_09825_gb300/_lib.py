@@ -23,7 +23,7 @@ FGT1D_FP32 = 1
 FGT1D_EXACT_SELF = 2
 FGT1D_F32X2 = 4
 MAX_TERMS = 8
-MAX_N = 14
+MAX_N = 16
 
 _lib = None
 
@@ -55,6 +55,10 @@ SIGNATURES = {
     "fgt1d_plan_set_tile": (_I, [_P, _I]),
     "fgt1d_plan_get_tile": (_I, [_P, _P]),
     "fgt1d_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _I, _P, _P, _P]),
+    "fgt1d_segment_execute": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "fgt1d_segment_compose": (_I, [_P, _I, _I, _P, _P]),
+    "fgt1d_segment_apply": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "fgt1d_measure_peaks": (_I, [_P, _P]),
     "fgt1d_check": (_I, [_P, _SZ, _P]),
     "fgt1d_strerror": (ctypes.c_char_p, [_I]),
     "fgt1d_version": (_I, []),

@@ -68,8 +68,10 @@ def build(verbose=False, extra_flags=()):
         if src.endswith(".cu"):
             cmd = [nvcc, "-c", s, "-o", o] + NVCC_FLAGS + vflags + list(extra_flags)
         else:
-            cmd = [nvcc, "-c", s, "-o", o, "-x", "c++", "-Xcompiler", "-fPIC", "-O2", "-std=c++17",
-                   "-I", INCLUDE, "-I", CSRC]
+            # no floating-point contraction on the host: the double-double SOE construction
+            # relies on exact two-sums, and x86 and Arm hosts then give the same nodes
+            cmd = [nvcc, "-c", s, "-o", o, "-x", "c++", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                   "-O2", "-std=c++17", "-I", INCLUDE, "-I", CSRC]
         jobs.append(cmd)
 
     def run(cmd):

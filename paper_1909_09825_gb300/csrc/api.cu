@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 
 #include "fgt1d_internal.h"
 #include "kernels.h"
@@ -87,6 +88,36 @@ int ws_ok(const void* ws, size_t ws_bytes, const Layout& L) {
     return FGT1D_OK;
 }
 
+// Bounded waits under test, without a GPU fault: FGT1D_SPIN_LIMIT_CYCLES (a positive
+// integer) replaces the default bound of one inter-block wait, and FGT1D_FAULT injects
+// a tile that never publishes -- "sweep_timeout" starts the forward sweep's tile counter
+// at 1, "sort_timeout" every digit pass's, so tile 0 is never processed and tile 1's
+// look-back wait runs out.  Read at every call.
+long long spin_limit_from_env() {
+    const char* v = std::getenv("FGT1D_SPIN_LIMIT_CYCLES");
+    if (!v) return kSpinLimitCycles;
+    const long long c = std::atoll(v);
+    return c > 0 ? c : kSpinLimitCycles;
+}
+enum Fault { kNoFault = 0, kSweepTimeout = 1, kSortTimeout = 2 };
+int fault_from_env() {
+    const char* v = std::getenv("FGT1D_FAULT");
+    if (!v) return kNoFault;
+    if (!std::strcmp(v, "sweep_timeout")) return kSweepTimeout;
+    if (!std::strcmp(v, "sort_timeout")) return kSortTimeout;
+    return kNoFault;
+}
+// Applied after the header is cleared: the tile counters that skip tile 0.
+cudaError_t inject_fault(char* ws, const Layout& L, cudaStream_t st) {
+    const int f = fault_from_env();
+    cudaError_t e = cudaSuccess;
+    if (f == kSweepTimeout) e = cudaMemsetAsync(ws + L.header + 64, 1, 1, st);  // forward sweep counter = 1
+    if (f == kSortTimeout)
+        for (int d = 0; d < kSortDigits && e == cudaSuccess; ++d)
+            e = cudaMemsetAsync(ws + L.header + 32 + 4 * d, 1, 1, st);  // each digit pass's counter = 1
+    return e;
+}
+
 SortArgs sort_args(const double* x, const double* y, int64_t N, char* ws, const Layout& L) {
     SortArgs a;
     a.x = x;
@@ -107,6 +138,7 @@ SortArgs sort_args(const double* x, const double* y, int64_t N, char* ws, const 
     a.desc_stride = (size_t)L.max_tiles * 256;
     a.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 32);
     a.status = reinterpret_cast<uint32_t*>(ws + L.header);
+    a.spin_limit = spin_limit_from_env();
     return a;
 }
 
@@ -248,6 +280,7 @@ SweepArgs sweep_args(const double* alpha, int64_t N, double* u, double* out2, ch
     w.bdesc = reinterpret_cast<TileDesc*>(ws + L.bdesc);
     w.tile_ctr = reinterpret_cast<uint32_t*>(ws + L.header + 64);
     w.status = reinterpret_cast<uint32_t*>(ws + L.header);
+    w.spin_limit = spin_limit_from_env();
     return w;
 }
 
@@ -257,10 +290,11 @@ SweepArgs sweep_args(const double* alpha, int64_t N, double* u, double* out2, ch
 int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
                  const ItemSource& src, double* u, double* out2, int ev, double* coinc, char* ws, const Layout& L,
                  cudaStream_t st, cudaEvent_t const* evs = nullptr, bool self = false,
-                 cudaEvent_t alpha_ready = nullptr) {
+                 cudaEvent_t alpha_ready = nullptr, double* boundary = nullptr) {
     auto rec = [&](int i) { return (evs && evs[i]) ? cudaEventRecord(evs[i], st) : cudaSuccess; };
     cudaError_t e = rec(0);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.zero_end, st);
+    if (e == cudaSuccess) e = inject_fault(ws, L, st);
     if (e != cudaSuccess) return FGT1D_ECUDA;
     Item* items = reinterpret_cast<Item*>(ws + L.items);
     int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
@@ -284,6 +318,8 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     else if (df && ev == 1) e = launch_sweeps_df(w, c, st, mid, shape_index(p, ev));
     else e = launch_sweeps_f64(w, c, st, mid, ev, shape_index(p, ev));
     if (e == cudaSuccess) e = rec(3);
+    // a segment's boundary record, read before the coincidence scan reuses the descriptors
+    if (e == cudaSuccess && boundary) e = launch_segment_boundary(w, M + N, p.n_e, boundary, st);
     if (e == cudaSuccess && coinc) {
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
@@ -304,6 +340,23 @@ int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const doubl
     // coincident pairs: add (1 - S_n(0)) times the coincident source strengths
     double* A = reinterpret_cast<double*>(ws + L.coinc);
     int r = run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, A, ws, L, st, evs, false, alpha_ready);
+    if (r) return r;
+    double s0 = 0.0;
+    for (int k = 0; k < p.n_e; ++k) s0 += p.w_re[k];
+    return cuda_status(launch_axpy(A, 1.0 - s0, M, u, st));
+}
+
+// A segment of a range-partitioned transform: the transform of its own points with zero
+// entering states (every size, so that a segment without targets still reports its
+// sources' boundary states), plus its boundary record.
+int run_segment(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
+                double* u, double* boundary, char* ws, const Layout& L, cudaStream_t st) {
+    if (!(p.flags & FGT1D_EXACT_SELF) || M == 0 || N == 0)
+        return run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, nullptr, ws, L, st, nullptr, false,
+                            nullptr, boundary);
+    double* A = reinterpret_cast<double*>(ws + L.coinc);
+    int r = run_pipeline(p, x, M, y, alpha, N, ItemSource(), u, nullptr, 1, A, ws, L, st, nullptr, false, nullptr,
+                         boundary);
     if (r) return r;
     double s0 = 0.0;
     for (int k = 0; k < p.n_e; ++k) s0 += p.w_re[k];
@@ -757,6 +810,118 @@ extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, cons
         return r;
     }
     return done(best);
+}
+
+// ---- range partition: segments of one transform ------------------------------------------
+extern "C" int fgt1d_segment_execute(fgt1d_plan plan, const double* x, int64_t M, const double* y,
+                                     const double* alpha, int64_t N, double* u, double* boundary, void* workspace,
+                                     size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(M, N) || !boundary) return FGT1D_EINVAL;
+    if (M > 0 && (!x || !u)) return FGT1D_EINVAL;
+    if (N > 0 && (!y || !alpha)) return FGT1D_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (M + N == 0) {  // no points: the empty record, and a clean status for fgt1d_check
+        cudaError_t e = launch_segment_empty(plan->n_e, boundary, st);
+        if (e == cudaSuccess && workspace && ws_bytes >= sizeof(uint32_t))
+            e = cudaMemsetAsync(workspace, 0, sizeof(uint32_t), st);
+        return cuda_status(e);
+    }
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    return run_segment(*plan, x, M, y, alpha, N, u, boundary, static_cast<char*>(workspace), L, st);
+}
+
+extern "C" int fgt1d_segment_compose(fgt1d_plan plan, int G, int g, const double* boundaries, double* carry) {
+    if (!plan || G < 1 || g < 0 || g >= G || !boundaries || !carry) return FGT1D_EINVAL;
+    const int n = plan->n_e;
+    const size_t stride = 4 * (size_t)n + 2;
+    const double s = 1.0 / std::sqrt(plan->delta);
+    // the segments must be ordered along the line: z_first <= z_last, and each segment
+    // starts at or after the previous non-empty one ends
+    double last = -INFINITY;
+    for (int j = 0; j < G; ++j) {
+        const double* b = boundaries + (size_t)j * stride;
+        const double zf = b[4 * n], zl = b[4 * n + 1];
+        if (std::isnan(zf) != std::isnan(zl)) return FGT1D_EINVAL;
+        if (std::isnan(zf)) continue;
+        if (!(zf <= zl) || !(last <= zf)) return FGT1D_EINVAL;
+        for (int i = 0; i < 4 * n; ++i)
+            if (!std::isfinite(b[i])) return FGT1D_EINVAL;
+        last = zl;
+    }
+    // span multiplier exp(-tau_k s d), d >= 0, computed directly from two coordinates
+    auto decay = [&](int k, double d, double& er, double& ei) {
+        const double mag = std::exp(-plan->tau_re[k] * s * d), ang = plan->tau_im[k] * s * d;
+        er = mag * std::cos(ang);
+        ei = -mag * std::sin(ang);
+    };
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (int k = 0; k < n; ++k) {
+        // forward: the state at the last point of the segments before g
+        double Fr = 0.0, Fi = 0.0, zl = nan;
+        for (int j = 0; j < g; ++j) {
+            const double* b = boundaries + (size_t)j * stride;
+            if (std::isnan(b[4 * n])) continue;
+            if (!std::isnan(zl)) {
+                double er, ei;
+                decay(k, b[4 * n + 1] - zl, er, ei);
+                const double t = er * Fr - ei * Fi;
+                Fi = er * Fi + ei * Fr;
+                Fr = t;
+            }
+            Fr += b[k];
+            Fi += b[n + k];
+            zl = b[4 * n + 1];
+        }
+        // backward: the state (inclusive) at the first point of the segments after g
+        double Gr = 0.0, Gi = 0.0, zf = nan;
+        for (int j = G - 1; j > g; --j) {
+            const double* b = boundaries + (size_t)j * stride;
+            if (std::isnan(b[4 * n])) continue;
+            if (!std::isnan(zf)) {
+                double er, ei;
+                decay(k, zf - b[4 * n], er, ei);
+                const double t = er * Gr - ei * Gi;
+                Gi = er * Gi + ei * Gr;
+                Gr = t;
+            }
+            Gr += b[2 * n + k];
+            Gi += b[3 * n + k];
+            zf = b[4 * n];
+        }
+        carry[k] = Fr;
+        carry[n + k] = Fi;
+        carry[2 * n + k] = Gr;
+        carry[3 * n + k] = Gi;
+        carry[4 * n] = zl;
+        carry[4 * n + 1] = zf;
+    }
+    return FGT1D_OK;
+}
+
+extern "C" int fgt1d_segment_apply(fgt1d_plan plan, int64_t M, int64_t N, const double* carry, double* u,
+                                   void* workspace, size_t ws_bytes, fgt1d_stream stream) {
+    if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
+    if (M == 0) return FGT1D_OK;
+    if (!carry || !u) return FGT1D_EINVAL;
+    Layout L = make_layout(M, N, 1, plan->n_e, plan->flags, true, false);
+    int r = ws_ok(workspace, ws_bytes, L);
+    if (r) return r;
+    SweepArgs w = sweep_args(nullptr, N, u, nullptr, static_cast<char*>(workspace), L);
+    SegmentConsts sc;
+    std::memset(&sc, 0, sizeof(sc));
+    sc.n_e = plan->n_e;
+    sc.s = 1.0 / std::sqrt(plan->delta);
+    sc.min_re_tau = INFINITY;
+    for (int k = 0; k < plan->n_e; ++k) {
+        sc.tau_re[k] = plan->tau_re[k];
+        sc.tau_im[k] = plan->tau_im[k];
+        sc.w_re[k] = plan->w_re[k];
+        sc.w_im[k] = plan->w_im[k];
+        sc.min_re_tau = std::min(sc.min_re_tau, plan->tau_re[k]);
+    }
+    return cuda_status(launch_carry_apply(w, M + N, sc, carry, u, static_cast<cudaStream_t>(stream)));
 }
 
 extern "C" int fgt1d_check(void* workspace, size_t ws_bytes, fgt1d_stream stream) {

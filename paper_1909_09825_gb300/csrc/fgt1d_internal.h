@@ -23,6 +23,8 @@ enum : uint32_t {
     kStatusNonFinite = 1u,
     kStatusTimeout = 2u,
     kStatusBadArg = 4u,     // a batch item with a bad delta or negative size
+    kStatusSortTimeout = 8u,  // a sort wait gave up: the sorted codes are not valid, and the
+                              // kernels that index outputs by them skip their work
 };
 
 // Degree limit of the per-point Taylor multiplier e^{-tau theta} and the number of

@@ -58,7 +58,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 16;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 static_assert(kSortTile == kTile, "sort tiles and item padding share one size");
-// Upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at 2 GHz).
+// Default upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at
+// 2 GHz); the launch arguments carry the bound in force (spin_limit).
 constexpr long long kSpinLimitCycles = 4000000000LL;
 
 struct SortPlan {
@@ -91,6 +92,7 @@ struct SortArgs {
     size_t desc_stride;   // max_tiles * 256
     uint32_t* tile_ctr;   // [8]
     uint32_t* status;
+    long long spin_limit = kSpinLimitCycles;  // bound of one look-back wait, SM cycles
 };
 
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
@@ -130,6 +132,7 @@ struct SweepArgs {
     uint32_t* status;
     int reuse = 0;          // 1: the multiplier table holds a bound geometry's multipliers
     int self = 0;           // 1: identical targets and sources (every point is both; FP64, FP32)
+    long long spin_limit = kSpinLimitCycles;  // bound of one look-back wait, SM cycles
 };
 
 // Evaluation channels of the sweeps: bit 0 values Re sum W (h+ + h-) into u, bit 1 the
@@ -161,6 +164,24 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
 // Identical points: u[point at sorted position p] += cf * F[last position of p's run of
 // equal coordinates], F from launch_coincidence (the run's total strength).
 cudaError_t launch_self_exact(const SweepArgs& a, const double* F, int64_t n, double cf, double* u, cudaStream_t st);
+
+// ---- range partition (segments of one transform) ----
+struct SegmentConsts {
+    int n_e;
+    double s;            // 1 / sqrt(delta)
+    double min_re_tau;   // smallest Re tau_k (the slowest decay)
+    double tau_re[FGT1D_MAX_TERMS], tau_im[FGT1D_MAX_TERMS];
+    double w_re[FGT1D_MAX_TERMS], w_im[FGT1D_MAX_TERMS];
+};
+// The segment's boundary record (4 n_e + 2 doubles) from the sweeps' descriptors and the
+// sorted keys of a single item of P points; must run before the descriptors are reused.
+cudaError_t launch_segment_boundary(const SweepArgs& a, int64_t P, int n_e, double* out, cudaStream_t st);
+// The record of a segment without points (zero states, NaN coordinates).
+cudaError_t launch_segment_empty(int n_e, double* out, cudaStream_t st);
+// u[target] += the contribution of the entering states in `carry` (device, 4 n_e + 2
+// doubles: Re/Im F_in, Re/Im G_in, z_prev, z_next; NaN coordinate = no neighbour).
+cudaError_t launch_carry_apply(const SweepArgs& a, int64_t P, const SegmentConsts& sc, const double* carry, double* u,
+                               cudaStream_t st);
 
 // fgt1d_execute on a caller-given workspace (checked against the layout size)
 int run_transform_in(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,

@@ -23,6 +23,8 @@
 //      rt * prod (w - q_k); residues in w are p(q_k) / prod_{l != k} (q_k - q_l);
 //   5. z_k = A (q_k - 1)^2 / (q_k + 1)^2, residue in z = residue in w * 4 z_k / (q_k^2 - 1).
 //
+// Orders n <= 14 run in FP64; n = 16 runs the same steps in double-double
+// (soe_cf_dd.cpp), as the paper builds its largest orders in extended precision.
 // One node of each conjugate pair is kept (Im t_k > 0) with weight W_k = 2 w_k
 // (Sec. 4).  E_n (eq. 3.1) is measured on x = 0, 1e5 log-spaced points in
 // [1e-5, 1e2] (the paper's grid) and uniform grids on [0, 12] and [0, 1e-3].
@@ -216,8 +218,38 @@ const CfBase& cf_base() {
     return b;
 }
 
+// The zeros of sum_j a[j] z^j (poly_zeros), interleaved (re, im), for the
+// double-double construction's starting values.
+std::vector<double> zeros_interleaved(const std::vector<double>& a) {
+    std::vector<double> out;
+    for (cd z : poly_zeros(a)) {
+        out.push_back(z.real());
+        out.push_back(z.imag());
+    }
+    return out;
+}
+
+}  // namespace
+
+// soe_cf_dd.cpp: the same construction in double-double arithmetic (n = 16).
+int build_cf_soe_dd(int n, std::vector<double> (*zeros_fp64)(const std::vector<double>&), double* tau_re,
+                    double* tau_im, double* w_re, double* w_im);
+
+namespace {
+
+// Orders above this are built in double-double (Sec. 3.3: beyond n = 14 the paper's
+// CF construction runs in extended precision).
+constexpr int kMaxNFp64 = 14;
+
 Soe build_cf_soe(int n) {
     Soe out;
+    if (n > kMaxNFp64) {
+        out.n = n;
+        out.n_e = n / 2;
+        out.status = build_cf_soe_dd(n, zeros_interleaved, out.tau_re, out.tau_im, out.w_re, out.w_im);
+        if (out.status == FGT1D_OK) out.E_n = measure_En(out);
+        return out;
+    }
     out.n = n;
     out.n_e = n / 2;
     const int K = kCfK;

@@ -442,8 +442,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
                     if ((x >> 62) == 0) {
                         const long long t0 = clock64();
                         while (((x = ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg])) >> 62) == 0) {
-                            if (clock64() - t0 > kSpinLimitCycles) {
-                                atomicOr(a.status, kStatusTimeout);
+                            if (clock64() - t0 > a.spin_limit) {
+                                atomicOr(a.status, kStatusTimeout | kStatusSortTimeout);
                                 x = kDescInc;
                                 break;
                             }

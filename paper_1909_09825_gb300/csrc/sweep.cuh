@@ -526,7 +526,7 @@ __device__ __forceinline__ void publish_inc(TileDesc* d, double ir, double ii) {
 // within a round the products of M are formed by a lane prefix scan.
 static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t tile, int dir, int64_t lo,
                                                    int64_t hi, int ne, int k, double& Cr, double& Ci,
-                                                   uint32_t* status) {
+                                                   uint32_t* status, long long spin_limit) {
     const int lane = threadIdx.x & 31;
     double Pr = 1.0, Pi = 0.0;  // product of the span multipliers of the tiles consumed so far
     Cr = 0.0;
@@ -543,7 +543,7 @@ static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t
             if (f == 0) {
                 const long long t0 = clock64();
                 while ((f = ld_volatile_u32(&d->flag)) == 0) {
-                    if (clock64() - t0 > kSpinLimitCycles) {
+                    if (clock64() - t0 > spin_limit) {
                         timed_out = true;
                         f = 2;
                         break;
@@ -826,7 +826,7 @@ __device__ __forceinline__ void tile_combine(const SweepArgs& a, TileDesc* desc,
     if (first_in_dir) {
         if (lane == 0) publish_inc(dd, Qr, Qi);
     } else {
-        look_back_warp(desc, tile, dir, lo, hi, NE, k, Cr, Ci, a.status);
+        look_back_warp(desc, tile, dir, lo, hi, NE, k, Cr, Ci, a.status, a.spin_limit);
         if (lane == 0) {
             double Ir, Ii;
             cfma<double>(Mr, Mi, Cr, Ci, Qr, Qi, Ir, Ii);
@@ -900,6 +900,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     if (tid == 0) {
         s_tile = atomicAdd(&a.tile_ctr[0], 1u);
         s_item = (int64_t)s_tile < *a.total_tiles ? item_of_tile(a.items, a.B, s_tile) : -1;
+        if (ld_volatile_u32(a.status) & kStatusSortTimeout) s_item = -1;  // sorted codes not valid
     }
     __syncthreads();
     if (s_item < 0) return;
@@ -1211,6 +1212,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
         const int64_t acq = atomicAdd(&a.tile_ctr[1], 1u);
         s_tilev = T_tot - 1 - acq;
         s_item = acq < T_tot ? item_of_tile(a.items, a.B, s_tilev) : -1;
+        if (ld_volatile_u32(a.status) & kStatusSortTimeout) s_item = -1;  // sorted codes not valid
     }
     __syncthreads();
     if (s_item < 0) return;

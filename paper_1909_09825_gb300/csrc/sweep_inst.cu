@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_self_exact(const SweepArgs a, const dou
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
+    if (*(volatile const uint32_t*)a.status & kStatusSortTimeout) return;  // sorted codes not valid
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[p];
         int64_t last = p;

@@ -194,3 +194,25 @@ def test_noalloc_rejects_null_arrays_before_the_gpu(L):
     assert f(None, v, 8, v, v, 8, v, None) == _lib.FGT1D_EINVAL            # plan
     assert f(p.handle, v, 40000, v, v, 30000, v, None) == _lib.FGT1D_ETOOLARGE
     assert f(p.handle, None, 0, None, None, 0, None, None) == _lib.FGT1D_OK  # nothing to do
+
+
+def test_cf_order_16_in_double_double(L):
+    """n = 16, built in double-double (Sec. 3.3 builds its largest orders in extended
+    precision): the claimed E_16 bounds |G - S_16| evaluated in extended precision on an
+    independent grid, the error keeps falling at the paper's geometric rate (about 7.5
+    per order, so E_14 / E_16 well above 20), the nodes keep Re tau > 0 with one of each
+    conjugate pair, and eps = 1e-12 now plans n = 16."""
+    import paper_1909_09825_gb300 as fgt
+    tau, W, E16 = fgt.soe_cf(16)
+    _, _, E14 = fgt.soe_cf(14)
+    assert len(tau) == 8 and E16 <= 2e-13
+    assert np.all(tau.real > 0) and np.all(tau.imag > 0)
+    x = np.concatenate([[0.0], np.linspace(0, 15, 150001), np.geomspace(1e-6, 1e-2, 20001)]).astype(np.longdouble)
+    t, w = tau.astype(np.clongdouble), W.astype(np.clongdouble)
+    S = np.real(np.sum(w[:, None] * np.exp(-t[:, None] * x[None, :]), axis=0))
+    true_err = float(np.max(np.abs(np.exp(-x * x / 4) - S)))
+    assert true_err <= E16
+    assert E14 / true_err > 20
+    assert abs(float(S[0]) - 1.0) <= E16
+    p = fgt.Plan(1e-3, 1e-12)
+    assert p.n == 16 and p.n_e == 8 and p.E_n == E16

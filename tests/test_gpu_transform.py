@@ -329,3 +329,19 @@ def test_presorted_inputs_vs_recurrence(cuda, prec):
     u = gpu_transform(plan, x, y, a)
     ref = oracle.recurrence(x, y, a, delta, tau, W)
     assert rel_inf(u, ref, a) <= {"fp64": TOL_ARITH64, "fp32": 5e-6}[prec]
+
+
+@pytest.mark.parametrize("delta", [1e-5, 1e-2, 1.0])
+def test_eps_1e12_order_16_vs_direct(cuda, delta):
+    """eps = 1e-12 plans the CF order n = 16 (n_e = 8, built in double-double, Sec. 3.3):
+    M = N = 2^20 uniform points against the direct Gauss sum (eq. 1.1) at 2000 sampled
+    targets plus the extremes, within 2 eps + 1e-13."""
+    M = N = 1 << 20
+    x, y, a = inputs.uniform(M, N, seed=61)
+    plan = fgt.Plan(delta, 1e-12)
+    assert plan.n == 16 and plan.n_e == 8
+    u = gpu_transform(plan, x, y, a)
+    rng = np.random.default_rng(62)
+    idx = np.unique(np.concatenate([[int(np.argmin(x)), int(np.argmax(x))], rng.choice(M, 2000, replace=False)]))
+    ref = oracle.direct(x[idx], y, a, delta, nthreads=0)
+    assert rel_inf(u[idx], ref, a) <= 2e-12 + 1e-13

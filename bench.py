@@ -56,7 +56,7 @@ def measure_peaks():
             "fp32_tflops": 2 * v[2] / 1e12, "fp32_fma_per_clk_per_sm": v[3],
             "sfu_ex2_per_s": v[4], "sfu_ex2_per_clk_per_sm": v[5],
             "sfu_sin_per_s": v[6], "sfu_sin_per_clk_per_sm": v[7], "sms": int(v[8]), "sm_mhz": v[9],
-            "how": "fgt1d_measure_peaks: 8 independent FMA/ex2/sin chains per thread, 8 x 256 threads per "
+            "how": "fgt1d_measure_peaks: 16 independent FMA/ex2/sin chains per thread, 8 x 256 threads per "
                    "SM, best of two CUDA-event-timed launches; SM clock from clock64 over globaltimer"}
 
 

@@ -316,7 +316,7 @@ int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, ui
                       void* workspace, size_t ws_bytes, fgt1d_stream stream);
 
 /* Measures the pipes that bound this library's kernels on the current device (no
- * counterpart in the paper): long independent chains of FP64 FMA, FP32 FMA and the
+ * counterpart in the paper): 16 independent chains per thread of FP64 FMA, FP32 FMA and the
  * special-function unit's ex2.approx and sin.approx on every SM, each timed with CUDA
  * events on `stream` (best of two after a warm-up launch).  out (host, >= 10 doubles):
  * out[0], out[1] FP64 FMA per second and per SM per clock cycle; out[2], out[3] the same

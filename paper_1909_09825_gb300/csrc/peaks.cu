@@ -17,8 +17,8 @@
 namespace fgt1d {
 namespace {
 
-constexpr int kChains = 8;
-constexpr int kIters = 4096;
+constexpr int kChains = 16;
+constexpr int kIters = 2048;
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads) k_peak_dfma(double seed, double* sin
 #pragma unroll
     for (int c = 0; c < kChains; ++c) v[c] = seed + c + threadIdx.x;
     const double b = 1.0 - 1e-9, d = 1e-9;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < kIters; ++i)
 #pragma unroll
         for (int c = 0; c < kChains; ++c) v[c] = fma(v[c], b, d);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_peak_ffma(float seed, float* sink,
 #pragma unroll
     for (int c = 0; c < kChains; ++c) v[c] = seed + c + threadIdx.x;
     const float b = 1.0f - 1e-6f, d = 1e-6f;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < kIters; ++i)
 #pragma unroll
         for (int c = 0; c < kChains; ++c) v[c] = __fmaf_rn(v[c], b, d);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_peak_sfu(float seed, float* sink, 
     float v[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) v[c] = seed * (c + 1) * 1e-3f;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < kIters; ++i)
 #pragma unroll
         for (int c = 0; c < kChains; ++c) {

@@ -595,6 +595,7 @@ static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t
 // finally by the output; strengths (Real); per-term exclusive thread prefixes (Real).
 // Per-point arrays are padded one slot per R points so that a warp reading one point
 // per thread (stride R) hits distinct banks.
+// The FP64 sweeps keep the scan region transposed for the serial warp scan (ScanIndex).
 template <typename Real, int NE, int T, int R>
 struct SweepSmem {
     static constexpr int TILE = T * R;
@@ -602,8 +603,58 @@ struct SweepSmem {
     static constexpr size_t z_off = 0;
     static constexpr size_t al_off = z_off + sizeof(double) * TP;
     static constexpr size_t scan_off = (al_off + sizeof(Real) * TP + 15) / 16 * 16;
-    static constexpr size_t bytes = scan_off + sizeof(Real) * 4 * NE * T;
+    static constexpr size_t scan_elems = std::is_same<Real, double>::value ? 4 * ((size_t)NE * T + 32)
+                                                                            : 4 * (size_t)NE * T;
+    static constexpr size_t bytes = scan_off + sizeof(Real) * scan_elems;
 };
+
+// FP64 scan region: component c (Re M, Im M, Re F, Im F) of thread position j (lane) in
+// warp w for term kk of the group is at c * 32 * S + j * S + kk * NW + w, S = NG NW + 1.
+// The threads of a warp (one term) write a column with stride S (about 2-way bank
+// conflicts); the lanes of the serial scan (one sequence each) read a row, consecutive.
+template <int NG, int NW>
+struct ScanIndex {
+    static constexpr int S = NG * NW + 1;
+    __device__ static __forceinline__ int at(int c, int j, int kk, int w) { return c * 32 * S + j * S + kk * NW + w; }
+};
+
+// Serial warp scan of the FP64 sweeps: the NW x (g1 - g0) sequences (one per warp and
+// term of the group) of 32 thread aggregates (M, F) each -- a thread's state map
+// h -> M h + F -- are combined by one lane each, in sweep order (lane 0 to 31 forward,
+// 31 to 0 backward).  Each entry is replaced by the exclusive composition of the
+// threads before it in sweep order and the warp's total goes to s_w.  Eight FP64
+// operations per thread and term, against forty for a shuffle scan over 32 lanes.
+template <int NG, int NW, bool kFwd, int NE>
+__device__ __forceinline__ void serial_warp_scan(double* s_scan, double (*s_w)[NW][4], int g0, int g1) {
+    using SI = ScanIndex<NG, NW>;
+    const int nseq = NW * (g1 - g0);
+    for (int q = threadIdx.x; q < nseq; q += blockDim.x) {
+        const int kk = q / NW, w = q % NW;
+        double Pr = 1.0, Pi = 0.0, Xr = 0.0, Xi = 0.0;
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = kFwd ? jj : 31 - jj;
+            double* e0 = s_scan + SI::at(0, j, kk, w);
+            double* e1 = s_scan + SI::at(1, j, kk, w);
+            double* e2 = s_scan + SI::at(2, j, kk, w);
+            double* e3 = s_scan + SI::at(3, j, kk, w);
+            const double mr = *e0, mi = *e1, fr = *e2, fi = *e3;
+            *e0 = Pr;
+            *e1 = Pi;
+            *e2 = Xr;
+            *e3 = Xi;
+            double nr, ni;
+            cfma<double>(mr, mi, Xr, Xi, fr, fi, nr, ni);  // X <- M X + F
+            Xr = nr;
+            Xi = ni;
+            cmul<double>(mr, mi, Pr, Pi, Pr, Pi);          // P <- M P
+        }
+        s_w[g0 + kk][w][0] = Pr;
+        s_w[g0 + kk][w][1] = Pi;
+        s_w[g0 + kk][w][2] = Xr;
+        s_w[g0 + kk][w][3] = Xi;
+    }
+}
 
 // Terms per group.  The value-channel sweeps run their terms in equal groups, each
 // with its own phases A-C, when the scan region of all NE terms would push the tile's
@@ -617,7 +668,8 @@ struct SweepGroup {
         if (EV != 1 || CO) return NE;
         for (int G = 1; G <= NE; ++G) {
             const int n = (NE + G - 1) / G;
-            if (SweepSmem<Real, 1, T, R>::scan_off + sizeof(Real) * 4 * (size_t)n * T <= kBudget) return n;
+            const size_t scan = std::is_same<Real, double>::value ? 4 * ((size_t)n * T + 32) : 4 * (size_t)n * T;
+            if (SweepSmem<Real, 1, T, R>::scan_off + sizeof(Real) * scan <= kBudget) return n;
         }
         return 1;
     }
@@ -1042,24 +1094,37 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 }
                 multiplier<Real>(c, k, hsp, thsp, Mr, Mi);
             }
+            if constexpr (kF64) {
+                // the thread's aggregate; the serial warp scan below combines them
+                using SI = ScanIndex<NG, NW>;
+                s_scan[SI::at(0, lane, k - g0, w)] = Mr;
+                s_scan[SI::at(1, lane, k - g0, w)] = Mi;
+                s_scan[SI::at(2, lane, k - g0, w)] = fr;
+                s_scan[SI::at(3, lane, k - g0, w)] = fi;
+            } else {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                Real Mor = shfl_up<Real>(Mr, o), Moi = shfl_up<Real>(Mi, o);
-                Real For = shfl_up<Real>(fr, o), Foi = shfl_up<Real>(fi, o);
-                if (lane >= o) {
-                    cfma<Real>(Mr, Mi, For, Foi, fr, fi, fr, fi);
-                    cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
+                for (int o = 1; o < 32; o <<= 1) {
+                    Real Mor = shfl_up<Real>(Mr, o), Moi = shfl_up<Real>(Mi, o);
+                    Real For = shfl_up<Real>(fr, o), Foi = shfl_up<Real>(fi, o);
+                    if (lane >= o) {
+                        cfma<Real>(Mr, Mi, For, Foi, fr, fi, fr, fi);
+                        cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
+                    }
+                }
+                Real Mxr = shfl_up<Real>(Mr, 1), Mxi = shfl_up<Real>(Mi, 1);
+                Real Fxr = shfl_up<Real>(fr, 1), Fxi = shfl_up<Real>(fi, 1);
+                if (lane == 0) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
+                Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+                sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
+                if (lane == 31) {
+                    s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+                    s_w[k][w][2] = real_to_f64<Real>(fr); s_w[k][w][3] = real_to_f64<Real>(fi);
                 }
             }
-            Real Mxr = shfl_up<Real>(Mr, 1), Mxi = shfl_up<Real>(Mi, 1);
-            Real Fxr = shfl_up<Real>(fr, 1), Fxi = shfl_up<Real>(fi, 1);
-            if (lane == 0) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
-            Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
-            sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
-            if (lane == 31) {
-                s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
-                s_w[k][w][2] = real_to_f64<Real>(fr); s_w[k][w][3] = real_to_f64<Real>(fi);
-            }
+        }
+        if constexpr (kF64) {
+            __syncthreads();
+            serial_warp_scan<NG, NW, true, NE>(reinterpret_cast<double*>(s_scan), s_w, g0, g1);
         }
         __syncthreads();
         // phase B: one lane per term joins the warps and the tiles
@@ -1077,8 +1142,15 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
         for (int k = g0; k < g1; ++k) {
             const Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
             Real fr, fi;
-            cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
-                       sc[2 * T + tid], sc[3 * T + tid], fr, fi);
+            if constexpr (kF64) {
+                using SI = ScanIndex<NG, NW>;
+                cfma<Real>(s_scan[SI::at(0, lane, k - g0, w)], s_scan[SI::at(1, lane, k - g0, w)], s_win[k][w][0],
+                           s_win[k][w][1], s_scan[SI::at(2, lane, k - g0, w)], s_scan[SI::at(3, lane, k - g0, w)], fr,
+                           fi);
+            } else {
+                cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                           sc[2 * T + tid], sc[3 * T + tid], fr, fi);
+            }
             const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
             const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
             auto eval = [&](int r) {
@@ -1332,24 +1404,37 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
             });
             Real Mr, Mi;
             multiplier<Real>(c, k, hsp, thsp, Mr, Mi);
+            if constexpr (kF64) {
+                // the thread's aggregate; the serial warp scan below combines them
+                using SI = ScanIndex<NG, NW>;
+                s_scan[SI::at(0, lane, k - g0, w)] = Mr;
+                s_scan[SI::at(1, lane, k - g0, w)] = Mi;
+                s_scan[SI::at(2, lane, k - g0, w)] = br;
+                s_scan[SI::at(3, lane, k - g0, w)] = bi;
+            } else {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);
-                Real For = shfl_down<Real>(br, o), Foi = shfl_down<Real>(bi, o);
-                if (lane + o < 32) {
-                    cfma<Real>(Mr, Mi, For, Foi, br, bi, br, bi);
-                    cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
+                for (int o = 1; o < 32; o <<= 1) {
+                    Real Mor = shfl_down<Real>(Mr, o), Moi = shfl_down<Real>(Mi, o);
+                    Real For = shfl_down<Real>(br, o), Foi = shfl_down<Real>(bi, o);
+                    if (lane + o < 32) {
+                        cfma<Real>(Mr, Mi, For, Foi, br, bi, br, bi);
+                        cmul<Real>(Mr, Mi, Mor, Moi, Mr, Mi);
+                    }
+                }
+                Real Mxr = shfl_down<Real>(Mr, 1), Mxi = shfl_down<Real>(Mi, 1);
+                Real Fxr = shfl_down<Real>(br, 1), Fxi = shfl_down<Real>(bi, 1);
+                if (lane == 31) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
+                Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
+                sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
+                if (lane == 0) {
+                    s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
+                    s_w[k][w][2] = real_to_f64<Real>(br); s_w[k][w][3] = real_to_f64<Real>(bi);
                 }
             }
-            Real Mxr = shfl_down<Real>(Mr, 1), Mxi = shfl_down<Real>(Mi, 1);
-            Real Fxr = shfl_down<Real>(br, 1), Fxi = shfl_down<Real>(bi, 1);
-            if (lane == 31) { Mxr = Real(1); Mxi = Real(0); Fxr = Real(0); Fxi = Real(0); }
-            Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
-            sc[tid] = Mxr; sc[T + tid] = Mxi; sc[2 * T + tid] = Fxr; sc[3 * T + tid] = Fxi;
-            if (lane == 0) {
-                s_w[k][w][0] = real_to_f64<Real>(Mr); s_w[k][w][1] = real_to_f64<Real>(Mi);
-                s_w[k][w][2] = real_to_f64<Real>(br); s_w[k][w][3] = real_to_f64<Real>(bi);
-            }
+        }
+        if constexpr (kF64) {
+            __syncthreads();
+            serial_warp_scan<NG, NW, false, NE>(reinterpret_cast<double*>(s_scan), s_w, g0, g1);
         }
         __syncthreads();
         for (int k = g0 + w; k < g1; k += NW)
@@ -1364,8 +1449,15 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
         for (int k = g0; k < g1; ++k) {
             const Real* sc = s_scan + (size_t)(k - g0) * 4 * T;
             Real br, bi;  // state at the first point of the next thread
-            cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
-                       sc[2 * T + tid], sc[3 * T + tid], br, bi);
+            if constexpr (kF64) {
+                using SI = ScanIndex<NG, NW>;
+                cfma<Real>(s_scan[SI::at(0, lane, k - g0, w)], s_scan[SI::at(1, lane, k - g0, w)], s_win[k][w][0],
+                           s_win[k][w][1], s_scan[SI::at(2, lane, k - g0, w)], s_scan[SI::at(3, lane, k - g0, w)], br,
+                           bi);
+            } else {
+                cfma<Real>(sc[tid], sc[T + tid], to_real<Real>(s_win[k][w][0]), to_real<Real>(s_win[k][w][1]),
+                           sc[2 * T + tid], sc[3 * T + tid], br, bi);
+            }
             const Real Wr = TermConsts<Real>::w_re(c, k), Wi = TermConsts<Real>::w_im(c, k);
             const Real Vr = TermConsts<Real>::v_re(c, k), Vi = TermConsts<Real>::v_im(c, k);
             const int deg = kTab ? 0 : taylor_degree<Real>(c, k, hw);

@@ -565,6 +565,13 @@ static __device__ __noinline__ void look_back_warp(const TileDesc* desc, int64_t
             mi = __ldcg(&d->M_im);
         }
         const unsigned incm = __ballot_sync(0xffffffffu, f == 2);
+        if (incm & 1u) {
+            // the nearest tile of this round has its inclusive value (the usual case: the
+            // previous tile finished its own look-back first): C += P v_0, no prefix scan
+            const double v0r = __shfl_sync(0xffffffffu, vr, 0), v0i = __shfl_sync(0xffffffffu, vi, 0);
+            cfma<double>(Pr, Pi, v0r, v0i, Cr, Ci, Cr, Ci);
+            break;
+        }
         const int last = incm ? __ffs(incm) - 1 : 31;
         // inclusive prefix product of M over lanes, then exclusive
         double Er = mr, Ei = mi;

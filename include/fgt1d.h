@@ -33,6 +33,13 @@
  *    returned by fgt1d_check, which synchronises the stream.
  *  - Return value: FGT1D_OK (0) or one of the FGT1D_E* codes below.
  *  - P = M + N must be below 2^31.  M = 0 is a no-op; N = 0 writes u = 0.
+ *  - Inter-block waits are bounded: a wait that runs past its bound (about 2 s of SM
+ *    clock by default) records FGT1D_ETIMEOUT for fgt1d_check and the kernels end.
+ *    Two environment variables, read at every call, exist to test this path without a
+ *    GPU fault: FGT1D_SPIN_LIMIT_CYCLES (a positive integer of SM clock cycles)
+ *    replaces the bound, and FGT1D_FAULT=sweep_timeout or sort_timeout makes one wait
+ *    of the forward sweep or of each sort pass run out (tile 0 is never processed).
+ *    After an expired sort wait the results are not written.  Leave both unset in use.
  */
 #ifndef FGT1D_H
 #define FGT1D_H

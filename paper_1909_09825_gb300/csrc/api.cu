@@ -21,7 +21,8 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // range to whole tiles, which adds at most one tile per item.
 struct Layout {
     size_t header = 0;       // status (u32 at 0), sort tile counters (8 u32 at 32), sweep tile
-                             // counters (2 u32 at 64), total tiles (i64 at 80), SortPlan at 128
+                             // counters (2 u32 at 64), total tiles (i64 at 80), equal-coordinate
+                             // flag (u32 at 88), geometry tag (u64 at 96), SortPlan at 128
     size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;
     size_t zero_end = 0;
     size_t items = 0;
@@ -311,6 +312,9 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
     w.self = self ? 1 : 0;
+    // with a coincidence scan to follow, the forward sweep records whether any two merged
+    // points share a coordinate (header word at 88, cleared above)
+    if (coinc && !self) w.ties = reinterpret_cast<uint32_t*>(ws + L.header + 88);
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;
@@ -323,6 +327,8 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     if (e == cudaSuccess && coinc) {
         e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
+        // all zero unless the scan runs (it returns at once when no coordinates coincide)
+        if (e == cudaSuccess && w.ties) e = cudaMemsetAsync(coinc, 0, sizeof(double) * (size_t)M, st);
         w.u = coinc;
         if (e == cudaSuccess) e = launch_coincidence(w, c, st);
     }

@@ -960,6 +960,7 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
         s_tile = atomicAdd(&a.tile_ctr[0], 1u);
         s_item = (int64_t)s_tile < *a.total_tiles ? item_of_tile(a.items, a.B, s_tile) : -1;
         if (ld_volatile_u32(a.status) & kStatusSortTimeout) s_item = -1;  // sorted codes not valid
+        if (CO && a.ties && ld_volatile_u32(a.ties) == 0) s_item = -1;   // no equal coordinates
     }
     __syncthreads();
     if (s_item < 0) return;
@@ -989,6 +990,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     // gaps of my R points, warp-wide largest gap
     Real thr[R];
     uint32_t hw = 0;
+    bool tie = false;  // a zero gap: two merged points share a coordinate
+    const bool track_ties = !CO && a.ties != nullptr;
     if (!reuse) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -998,8 +1001,10 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
                 t = gap_real<Real>(i > 0 ? s_z[pad<R>(i - 1)] : zprev, s_z[pad<R>(i)], sc);
             thr[r] = t;
             hw = max(hw, theta_hw<Real>(t));
+            if (track_ties && i < nvalid && (i > 0 || !first) && t == Real(0)) tie = true;
         }
         hw = __reduce_max_sync(0xffffffffu, hw);
+        if (track_ties && __any_sync(0xffffffffu, tie) && lane == 0) atomicOr(a.ties, 1u);
     }
     Real thsp = 0;
     if (i0 < nvalid && (!first || i0 > 0))

@@ -312,9 +312,9 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     if (e != cudaSuccess) return FGT1D_ECUDA;
     SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
     w.self = self ? 1 : 0;
-    // with a coincidence scan to follow, the forward sweep records whether any two merged
-    // points share a coordinate (header word at 88, cleared above)
-    if (coinc && !self) w.ties = reinterpret_cast<uint32_t*>(ws + L.header + 88);
+    // gradient sweeps with a coincidence scan to follow: the forward sweep records whether
+    // any two merged points share a coordinate (header word at 88, cleared above)
+    if (coinc && !self && (ev & 2)) w.ties = reinterpret_cast<uint32_t*>(ws + L.header + 88);
     const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
     SweepConsts c = make_consts(p);
     cudaEvent_t mid = evs ? evs[2] : nullptr;

@@ -132,9 +132,9 @@ struct SweepArgs {
     uint32_t* status;
     int reuse = 0;          // 1: the multiplier table holds a bound geometry's multipliers
     int self = 0;           // 1: identical targets and sources (every point is both; FP64, FP32)
-    // equal-coordinate flag (may be null): the forward sweep sets it when two merged points
-    // share a coordinate; the coincidence scan, whose output is then all zero, returns at
-    // once while it is clear
+    // equal-coordinate flag (may be null; gradient sweeps only): the forward sweep of the
+    // derivative channel sets it when two merged points share a coordinate; the
+    // coincidence scan, whose output is then all zero, returns at once while it is clear
     uint32_t* ties = nullptr;
     long long spin_limit = kSpinLimitCycles;  // bound of one look-back wait, SM cycles
 };

@@ -991,7 +991,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     Real thr[R];
     uint32_t hw = 0;
     bool tie = false;  // a zero gap: two merged points share a coordinate
-    const bool track_ties = !CO && a.ties != nullptr;
+    // (gradient sweeps only: the value channel's kernels stay free of this check)
+    const bool track_ties = !CO && (EV & 2) != 0 && a.ties != nullptr;
     if (!reuse) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -12,9 +12,12 @@
 // B every y_j > x_i (eq. 4.4).
 //
 // GB300 design.  Each recurrence is an associative scan of affine maps h -> m h + a.
-// A CTA owns a tile of T*R consecutive points; each thread runs R consecutive points
-// sequentially (work-efficient), a warp shuffle scan joins the threads of a warp, and
-// one lane per term joins the warps and the tiles.  Per tile the kernel runs
+// The 128-thread shape is persistent: as many CTAs as fit on the GPU, each taking tiles in
+// sweep order from an atomic counter until none is left; the 256-thread shape runs one
+// CTA per tile (both measured faster that way).  A tile is T*R consecutive points;
+// each thread runs R consecutive points sequentially (work-efficient), the threads of a
+// warp are joined by a serial scan of their aggregates in shared memory (FP64) or a
+// shuffle scan (FP32, double-float), and one lane per term joins the warps and the tiles.  Per tile the kernel runs
 //   phase A  per term: multipliers, thread aggregates, warp scans (exclusive prefixes
 //            kept in shared memory);
 //   phase B  per term (one warp each): combine the warp totals, publish the tile
@@ -956,6 +959,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
     static_assert(TILE == kTile, "a sweep tile is one item tile");
     __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // persistent: each CTA takes tiles in order from the counter until none is left
+    for (;;) {
     if (tid == 0) {
         s_tile = atomicAdd(&a.tile_ctr[0], 1u);
         s_item = (int64_t)s_tile < *a.total_tiles ? item_of_tile(a.items, a.B, s_tile) : -1;
@@ -1264,6 +1269,9 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_fwd(co
             if constexpr ((EV & 2) != 0) static_cast<Real*>(a.fwd2)[base + i] = s_acc2[pad<R>(i)];
         }
     }
+    if constexpr (T >= 256) return;  // one tile per CTA (the launch gives every tile a CTA)
+    __syncthreads();  // the next tile's staging overwrites the shared arrays
+    }
 }
 
 template <typename Real, int NE, int T, int R, int EV>
@@ -1292,6 +1300,8 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
     __shared__ int s_item;
     __shared__ int64_t s_tilev;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // persistent: each CTA takes tiles in reverse order from the counter until none is left
+    for (;;) {
     if (tid == 0) {
         const int64_t T_tot = *a.total_tiles;
         const int64_t acq = atomicAdd(&a.tile_ctr[1], 1u);
@@ -1551,6 +1561,9 @@ __global__ void __launch_bounds__(T, SweepMinBlocks<Real>::value) k_sweep_bwd(co
             if constexpr ((EV & 2) != 0)
                 a.out2[t] = s * real_to_f64<Real>(static_cast<const Real*>(a.fwd2)[p] + s_acc2[pad<R>(i)]);
         }
+    }
+    if constexpr (T >= 256) return;  // one tile per CTA (the launch gives every tile a CTA)
+    __syncthreads();  // the next tile's staging overwrites the shared arrays
     }
 }
 

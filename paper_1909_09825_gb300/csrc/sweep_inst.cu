@@ -34,7 +34,7 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
     auto kf = k_sweep_fwd<double, 1, kT64, kR64, 1, true>;
     cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kf<<<(unsigned)a.max_tiles, kT64, smem, st>>>(a, c);
+    kf<<<persistent_grid(kf, kT64, smem, a.max_tiles), kT64, smem, st>>>(a, c);
     return cudaGetLastError();
 }
 

@@ -216,3 +216,23 @@ def test_cf_order_16_in_double_double(L):
     assert abs(float(S[0]) - 1.0) <= E16
     p = fgt.Plan(1e-3, 1e-12)
     assert p.n == 16 and p.n_e == 8 and p.E_n == E16
+
+
+def test_measure_peaks_rejects_null_output(L):
+    from paper_1909_09825_gb300 import _lib
+    assert L.fgt1d_measure_peaks(None, None) == _lib.FGT1D_EINVAL
+
+
+def test_segment_entry_points_check_arguments_on_the_host(L):
+    """The segment calls reject bad arguments before any GPU work."""
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    p = fgt.Plan(1e-3, 1e-6)
+    v = (ctypes.c_double * 64)()
+    assert L.fgt1d_segment_execute(p.handle, v, 4, v, v, 4, v, None, v, 0, None) == _lib.FGT1D_EINVAL  # boundary
+    assert L.fgt1d_segment_execute(p.handle, None, 4, v, v, 4, v, v, v, 0, None) == _lib.FGT1D_EINVAL  # x
+    assert L.fgt1d_segment_execute(p.handle, v, 4, v, v, 4, v, v, None, 0, None) == _lib.FGT1D_EWORKSPACE
+    assert L.fgt1d_segment_apply(p.handle, 4, 4, None, v, v, 0, None) == _lib.FGT1D_EINVAL
+    assert L.fgt1d_segment_apply(p.handle, 0, 4, None, None, None, 0, None) == _lib.FGT1D_OK  # no targets
+    assert L.fgt1d_segment_compose(p.handle, 2, 2, v, v) == _lib.FGT1D_EINVAL                    # g out of range
+    assert L.fgt1d_segment_compose(None, 1, 0, v, v) == _lib.FGT1D_EINVAL

@@ -298,7 +298,7 @@ def main():
                                             "+2 per point" % C_CE,
                 "traffic": None}
     # the backward sweep (4 + 2 M/P per point and term) and the whole transform
-    # (n_e (C_ce + 20) FP64 ops per point, the survey's count) against the same peak
+    # (n_e (C_ce + 20) FP64 ops per point, C_ce fixed before tuning) against the same peak
     bwd_ops = P * n_e * (4 + 2.0 * M / P)
     bwd_ach = 2 * bwd_ops / (stages["bwd_sweep_ms"] * 1e-3) / 1e12
     whole_ach = 2 * P * n_e * (C_CE + 20) / (ms * 1e-3) / 1e12

@@ -224,7 +224,11 @@ int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads);
  * execute calls after it).  *threads_out (may be NULL) receives the chosen shape and
  * ms_out (may be NULL, room for 2) the mean milliseconds of shapes 128 and 256.  If
  * the environment variable FGT1D_TILE_THREADS is 128 or 256 that shape is taken
- * without timing (ms_out gets -1).  Errors: those of the execute call, or the device
+ * without timing (ms_out gets -1).  If FGT1D_TUNE_CACHE names a file, a choice stored
+ * there for the same precision, n_e, floor(log2(M_total + N_total)) and kind (single or
+ * batched) is taken without timing (ms_out gets -1), and a timed choice is appended to
+ * it (text lines "<precision flags> <n_e> <log2 size> <batched> <threads> <ms>"; the
+ * file belongs to one GPU model).  Errors: those of the execute call, or the device
  * status as fgt1d_check reports it; the plan keeps its previous shape on error. */
 int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off, const double* delta,
                    const double* x, int64_t M_total, const double* y, const double* alpha, int64_t N_total,

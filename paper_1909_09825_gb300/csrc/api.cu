@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
@@ -758,6 +759,51 @@ extern "C" int fgt1d_plan_get_tile(fgt1d_plan plan, int* threads) {
     return FGT1D_OK;
 }
 
+namespace fgt1d {
+namespace {
+
+// Autotuner cache (FGT1D_TUNE_CACHE names a text file, one choice per line:
+// "<precision> <n_e> <log2 of M_total + N_total> <batched> <threads> <ms>").  A line
+// matching the workload's key gives the tile shape without timing; a timed choice is
+// appended.  The file belongs to one GPU model.
+struct TuneKey {
+    unsigned prec;
+    int n_e, lg, batched;
+};
+TuneKey tune_key(const fgt1d_plan_s& p, int64_t P, bool batched) {
+    int lg = 0;
+    while (lg < 62 && (int64_t(1) << (lg + 1)) <= P) ++lg;
+    return TuneKey{p.flags & (FGT1D_FP32 | FGT1D_F32X2), p.n_e, lg, batched ? 1 : 0};
+}
+int tune_cache_lookup(const TuneKey& k) {
+    const char* path = std::getenv("FGT1D_TUNE_CACHE");
+    if (!path || !*path) return 0;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return 0;
+    unsigned prec;
+    int ne, lg, b, t;
+    double ms;
+    int found = 0;
+    char line[256];
+    while (!found && std::fgets(line, sizeof(line), f))
+        if (std::sscanf(line, "%u %d %d %d %d %lf", &prec, &ne, &lg, &b, &t, &ms) == 6 && prec == k.prec &&
+            ne == k.n_e && lg == k.lg && b == k.batched && (t == 128 || t == 256))
+            found = t;
+    std::fclose(f);
+    return found;
+}
+void tune_cache_store(const TuneKey& k, int threads, float ms) {
+    const char* path = std::getenv("FGT1D_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%u %d %d %d %d %.4f\n", k.prec, k.n_e, k.lg, k.batched, threads, (double)ms);
+    std::fclose(f);
+}
+
+}  // namespace
+}  // namespace fgt1d
+
 extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, const int64_t* y_off, const double* delta,
                               const double* x, int64_t M_total, const double* y, const double* alpha, int64_t N_total,
                               double* u, void* workspace, size_t ws_bytes, int reps, fgt1d_stream stream,
@@ -777,6 +823,8 @@ extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, cons
         if (t == 128 || t == 256) return done(t);
     }
     if (M_total == 0 || N_total == 0) return done(prev);  // nothing runs on the device
+    const TuneKey key = tune_key(*plan, M_total + N_total, x_off != nullptr);
+    if (const int cached = tune_cache_lookup(key)) return done(cached);
     auto run = [&]() {
         return x_off ? fgt1d_execute_batched(plan, B, x_off, y_off, delta, x, M_total, y, alpha, N_total, u, workspace,
                                              ws_bytes, stream)
@@ -815,6 +863,7 @@ extern "C" int fgt1d_autotune(fgt1d_plan plan, int B, const int64_t* x_off, cons
         plan->tile_threads = prev;
         return r;
     }
+    tune_cache_store(key, best, best_ms);
     return done(best);
 }
 

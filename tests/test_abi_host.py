@@ -236,3 +236,22 @@ def test_segment_entry_points_check_arguments_on_the_host(L):
     assert L.fgt1d_segment_apply(p.handle, 0, 4, None, None, None, 0, None) == _lib.FGT1D_OK  # no targets
     assert L.fgt1d_segment_compose(p.handle, 2, 2, v, v) == _lib.FGT1D_EINVAL                    # g out of range
     assert L.fgt1d_segment_compose(None, 1, 0, v, v) == _lib.FGT1D_EINVAL
+
+
+def test_autotune_takes_a_cached_choice_without_timing(L, tmp_path, monkeypatch):
+    """With FGT1D_TUNE_CACHE naming a file that holds a choice for this workload's key
+    (precision flags, n_e, floor(log2(M + N)), single/batched), fgt1d_autotune takes it
+    without running anything on the device (ms_out stays -1); other keys do not match."""
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    p = fgt.Plan(1e-3, 1e-6)  # FP64, n_e = 5
+    cache = tmp_path / "tune.txt"
+    cache.write_text("0 5 10 1 256 1.0\n1 5 10 0 256 1.0\n0 5 10 0 128 3.25\n")
+    monkeypatch.setenv("FGT1D_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("FGT1D_TILE_THREADS", raising=False)
+    v = (ctypes.c_double * 4)()  # never read on a cache hit
+    chosen, ms = ctypes.c_int(), (ctypes.c_float * 2)()
+    rc = L.fgt1d_autotune(p.handle, 1, None, None, None, v, 1000, v, v, 1000, v, v, 1 << 20, 2, None,
+                          ctypes.byref(chosen), ms)
+    assert rc == _lib.FGT1D_OK and chosen.value == 128 and p.tile_threads == 128
+    assert list(ms) == [-1.0, -1.0]

@@ -259,6 +259,24 @@ def test_autotune_picks_the_faster_shape(cuda):
     assert rel_inf(u[idx], oracle.direct(x[idx], y, a, delta), a) <= 2e-6 + 1e-13
 
 
+def test_autotune_cache_file_round_trip(cuda, tmp_path, monkeypatch):
+    """With FGT1D_TUNE_CACHE set, the first autotune times both shapes and appends its
+    choice; a second plan of the same key reads it back without timing."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("FGT1D_TUNE_CACHE", str(path))
+    x, y, a = inputs.uniform(200000, 200000, seed=5)
+    X, Y, A = (torch.from_numpy(v).to(cuda) for v in (x, y, a))
+    first = fgt.Plan(1e-4, 1e-6).autotune(X, Y, A, reps=2)
+    assert first[128] > 0 and first[256] > 0
+    lines = path.read_text().split()
+    assert len(lines) == 6 and int(lines[4]) == first["chosen"]
+    plan = fgt.Plan(1e-4, 1e-6)
+    second = plan.autotune(X, Y, A, reps=2)
+    assert second["chosen"] == first["chosen"] == plan.tile_threads
+    assert second[128] < 0 and second[256] < 0  # nothing timed
+    assert len(path.read_text().split()) == 6  # nothing appended
+
+
 def test_empty_inputs(cuda):
     plan = fgt.Plan(1e-3, 1e-6)
     d = cuda

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -25,9 +26,10 @@ struct Layout {
                              // counters (2 u32 at 64), total tiles (i64 at 80), equal-coordinate
                              // flag (u32 at 88), geometry tag (u64 at 96), SortPlan at 128
     size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;
+    size_t sort_aux = 0;     // PrefixPlan (256 B), then the per-item prefix maps
     size_t zero_end = 0;
     size_t items = 0;
-    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0, fwd2 = 0, coinc = 0;
+    size_t keysA = 0, keysB = 0, valsA = 0, valsB = 0, mult = 0, fwd = 0, fwd2 = 0, coinc = 0, pre = 0;
     size_t gD = 0, gA = 0, gx = 0, gy = 0, parts = 0;   // gradients
     size_t hx = 0, hy = 0, ha = 0, hu = 0;              // device copies of host arrays
     size_t total = 0;
@@ -47,6 +49,7 @@ Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sw
     L.hist = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256 * (size_t)B);
     L.offs = off; off += align_up(sizeof(uint32_t) * kSortDigits * 256 * (size_t)B);
     L.sort_desc = off; off += align_up(sizeof(uint64_t) * kSortDigits * (size_t)L.max_tiles * 256);
+    L.sort_aux = off; off += align_up(256 + sizeof(PrefixMap) * (size_t)B);
     const int64_t st = sweeps ? L.max_tiles : 0;
     L.fdesc = off; off += align_up(sizeof(TileDesc) * (size_t)st * (size_t)n_e);
     L.bdesc = off; off += align_up(sizeof(TileDesc) * (size_t)st * (size_t)n_e);
@@ -61,6 +64,13 @@ Layout make_layout(int64_t M, int64_t N, int B, int n_e, unsigned flags, bool sw
         if (!(flags & FGT1D_FP32)) { L.mult = off; off += align_up(sizeof(double2) * (size_t)n_e * Pp); }
         L.fwd = off; off += align_up(sizeof(double) * Pp);
         if (flags & FGT1D_EXACT_SELF) { L.coinc = off; off += align_up(sizeof(double) * (size_t)M); }
+    }
+    // the prefix sort's scratch (two arrays of 32-bit keys): the forward partial sums,
+    // which the sweeps write after the sort, or a region of its own
+    if (sweeps) {
+        L.pre = L.fwd;
+    } else {
+        L.pre = off; off += align_up(sizeof(uint32_t) * 2 * Pp);
     }
     if (grad) {
         const size_t mx = (size_t)std::max(M, N);
@@ -93,7 +103,7 @@ int ws_ok(const void* ws, size_t ws_bytes, const Layout& L) {
 // Bounded waits under test, without a GPU fault: FGT1D_SPIN_LIMIT_CYCLES (a positive
 // integer) replaces the default bound of one inter-block wait, and FGT1D_FAULT injects
 // a tile that never publishes -- "sweep_timeout" starts the forward sweep's tile counter
-// at 1, "sort_timeout" every digit pass's, so tile 0 is never processed and tile 1's
+// at 1, "sort_timeout" every prefix digit pass's, so tile 0 is never processed and tile 1's
 // look-back wait runs out.  Read at every call.
 long long spin_limit_from_env() {
     const char* v = std::getenv("FGT1D_SPIN_LIMIT_CYCLES");
@@ -115,16 +125,20 @@ cudaError_t inject_fault(char* ws, const Layout& L, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (f == kSweepTimeout) e = cudaMemsetAsync(ws + L.header + 64, 1, 1, st);  // forward sweep counter = 1
     if (f == kSortTimeout)
-        for (int d = 0; d < kSortDigits && e == cudaSuccess; ++d)
-            e = cudaMemsetAsync(ws + L.header + 32 + 4 * d, 1, 1, st);  // each digit pass's counter = 1
+        for (int d = 0; d < kPrefixDigits && e == cudaSuccess; ++d)  // each prefix pass's counter = 1
+            e = cudaMemsetAsync(ws + L.sort_aux + offsetof(PrefixPlan, pass_ctr) + 4 * d, 1, 1, st);
     return e;
 }
 
-SortArgs sort_args(const double* x, const double* y, int64_t N, char* ws, const Layout& L) {
+SortArgs sort_args(const double* x, int64_t M, const double* y, int64_t N, char* ws, const Layout& L) {
     SortArgs a;
     a.x = x;
     a.y = y;
     a.N = N;
+    a.M = M;
+    a.Ppad = L.Ppad;
+    a.pplan = reinterpret_cast<PrefixPlan*>(ws + L.sort_aux);
+    a.maps = reinterpret_cast<PrefixMap*>(ws + L.sort_aux + 256);
     a.items = reinterpret_cast<const Item*>(ws + L.items);
     a.B = L.B;
     a.total_tiles = reinterpret_cast<const int64_t*>(ws + L.header + 80);
@@ -133,6 +147,7 @@ SortArgs sort_args(const double* x, const double* y, int64_t N, char* ws, const 
     a.keysB = reinterpret_cast<uint64_t*>(ws + L.keysB);
     a.valsA = reinterpret_cast<uint32_t*>(ws + L.valsA);
     a.valsB = reinterpret_cast<uint32_t*>(ws + L.valsB);
+    a.pre = reinterpret_cast<uint32_t*>(ws + L.pre);
     a.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
     a.offs = reinterpret_cast<uint32_t*>(ws + L.offs);
     a.plan = reinterpret_cast<SortPlan*>(ws + L.header + 128);
@@ -305,7 +320,7 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
                                  L.max_tiles, M, N, st)
                   : launch_item_single(M, N, p.delta, items, total_tiles, st);
     if (e != cudaSuccess) return FGT1D_ECUDA;
-    SortArgs sa = sort_args(x, y, N, ws, L);
+    SortArgs sa = sort_args(x, M, y, N, ws, L);
     e = launch_sort(sa, st);
     if (e == cudaSuccess) e = rec(1);
     // strengths copied on another stream meanwhile (the sort does not read them)
@@ -588,7 +603,7 @@ extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, in
     if (launch_item_single(M, N, 1.0, reinterpret_cast<Item*>(ws + L.items),
                            reinterpret_cast<int64_t*>(ws + L.header + 80), st) != cudaSuccess)
         return FGT1D_ECUDA;
-    SortArgs sa = sort_args(x, y, N, ws, L);
+    SortArgs sa = sort_args(x, M, y, N, ws, L);
     if (launch_sort(sa, st) != cudaSuccess) return FGT1D_ECUDA;
     return cuda_status(launch_copy_perm(sa, M + N, perm, st));
 }
@@ -691,7 +706,7 @@ extern "C" int fgt1d_geometry_bind(fgt1d_plan plan, const double* x, int64_t M, 
     int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
     if (e == cudaSuccess)
         e = launch_item_single(M, N, plan->delta, reinterpret_cast<Item*>(ws + L.items), total_tiles, st);
-    SortArgs sa = sort_args(x, y, N, ws, L);
+    SortArgs sa = sort_args(x, M, y, N, ws, L);
     if (e == cudaSuccess) e = launch_sort(sa, st);
     SweepArgs w = sweep_args(nullptr, N, nullptr, nullptr, ws, L);
     SweepConsts c = make_consts(*plan);

@@ -53,17 +53,21 @@ cudaError_t launch_item_single(int64_t M, int64_t N, double delta, Item* items, 
                                cudaStream_t st);
 
 // ---- sort (steps a1-a2) ----
-constexpr int kSortDigits = 8;      // 8-bit digits of a 64-bit key
+constexpr int kSortDigits = 8;      // 8-bit digits of a 64-bit key (the full sort)
+constexpr int kPrefixDigits = 4;    // 8-bit digits of a 32-bit prefix key (the prefix sort)
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 16;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 static_assert(kSortTile == kTile, "sort tiles and item padding share one size");
+// Longest run of equal prefix keys that the fix-up sorts (one warp per run); a longer
+// run with coordinates out of order sends the sort to the full 64-bit passes.
+constexpr int kRunMax = 32;
 // Default upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at
 // 2 GHz); the launch arguments carry the bound in force (spin_limit).
 constexpr long long kSpinLimitCycles = 4000000000LL;
 
 struct SortPlan {
-    uint32_t active[kSortDigits];
+    uint32_t active[kSortDigits];   // full sort: digit d runs a pass
     int32_t src[kSortDigits];   // -1: keys generated from x/y; 0: buffer A; 1: buffer B
     int32_t dst[kSortDigits];
     int32_t final_buf;          // buffer (0 = A, 1 = B) that holds the sorted keys/indices
@@ -73,24 +77,56 @@ struct SortPlan {
 };
 static_assert(128 + sizeof(SortPlan) <= 256, "the sort plan sits in the workspace header");
 
+// The prefix sort: 32-bit keys that are a non-decreasing function of the coordinate
+// within each item (fixed point over the item's coordinate range), sorted by four
+// digit passes that carry the full 64-bit keys and the codes.  Runs of equal prefix keys
+// then hold merged-index order and are fixed up; too long a run with coordinates out
+// of order sets `fallback` and the full sort runs from the start.
+struct PrefixPlan {
+    uint32_t active[kPrefixDigits];
+    // buffers (prefix keys, full keys, codes): 0 = (pre, keysA, valsA), 1 = (pre + Ppad,
+    // keysB, valsB); the histogram pass writes buffer 1
+    int32_t src[kPrefixDigits];
+    int32_t dst[kPrefixDigits];
+    int32_t final_buf;            // buffer of the sorted points
+    uint32_t mask;                // bit d: some item has more than one populated bucket in prefix digit d
+    uint32_t fallback;
+    uint32_t nruns;               // runs listed for the fix-up (in the other buffer's prefix words)
+    uint32_t pass_ctr[kPrefixDigits];
+};
+
+// Per-item prefix map: prefix(z) = (Q(z) - qlo) >> sh, Q(z) = sign(z) floor(|z| / 2^(eh - 1075))
+// (eh = the larger biased exponent of the item's extreme coordinates).  Built in place
+// of the item's coordinate range (~min key, max key).
+struct PrefixMap {
+    int64_t qlo;
+    int32_t eh;
+    int32_t sh;
+};
+
 struct SortArgs {
     const double* x;
     const double* y;
     int64_t N;            // total number of sources (targets are coded N + i)
+    int64_t M;            // total number of targets (codes below N + M are points)
     const Item* items;
     int B;
     const int64_t* total_tiles;  // device scalar
     int64_t max_tiles;    // grid size of the tile kernels (upper bound of *total_tiles)
+    int64_t Ppad;         // max_tiles * kTile
     uint64_t* keysA;
     uint64_t* keysB;
     uint32_t* valsA;
     uint32_t* valsB;
+    uint32_t* pre;        // [2][Ppad] prefix keys of the prefix sort's buffers 0 and 1 (scratch)
     uint32_t* hist;       // [B][8][256] per-item digit counts
     uint32_t* offs;       // [B][8][256] per-item bucket starts (merged positions)
     SortPlan* plan;
+    PrefixPlan* pplan;
+    PrefixMap* maps;      // [B], zeroed before the sort
     uint64_t* desc;       // [8][desc_stride] look-back words
     size_t desc_stride;   // max_tiles * 256
-    uint32_t* tile_ctr;   // [8]
+    uint32_t* tile_ctr;   // [8] (full passes)
     uint32_t* status;
     long long spin_limit = kSpinLimitCycles;  // bound of one look-back wait, SM cycles
 };

@@ -6,15 +6,35 @@
 // key (-0.0 is folded onto +0.0).  A stable sort by key then puts equal coordinates in
 // merged-index order: sources before targets, as eq. 4.4 needs (y_j <= x_i goes to h+).
 //
-// GB300 design: one histogram pass counts all eight 8-bit digits at once (per-thread
-// run-length counting keeps the near-constant high digits off the shared atomics);
-// a one-block kernel turns the counts into bucket offsets and a device-side pass plan
-// that skips digits with a single populated bucket; then one "onesweep" kernel per
-// digit ranks a 4096-key tile in shared memory (ballot-based warp ranking), finds the
-// tile's global offsets by decoupled look-back over the preceding tiles, and writes
-// keys and merged indices out through a shared-memory reorder so that every bucket
-// run is written contiguously.  The pass plan lives on the device, so the whole sort
-// is launched without a host round trip (and can be captured in a CUDA graph).
+// GB300 design.  The order only needs as many key bits as separate the points, so the
+// sort runs on a 32-bit prefix key: per item, the fixed-point value of the coordinate
+// on the grid 2^(eh - 1075) (eh = the larger exponent of the item's extreme
+// coordinates), less that of the smallest coordinate, shifted right until the item's
+// range fits 32 bits.  It is integer arithmetic on the coordinate's bits and a
+// non-decreasing function of the coordinate, so sorting by it leaves only runs of equal
+// prefixes in merged-index order; for 2^27 uniform points in 2^32 bins about 3 % of
+// the points share a prefix.  Stages:
+//   range   per-item smallest and largest key (one read of x and y);
+//   hist    the four prefix-digit histograms per item and the presorted check; writes
+//           each point's prefix key, full key and merged code (buffer 1);
+//   plan    bucket offsets and the digits with more than one populated bucket;
+//   4 x     a "onesweep" digit pass on the prefix keys, with the full keys and codes as
+//           payload: each 4096-key tile is ranked in shared memory (ballot-based warp
+//           ranking), finds its global offsets by decoupled look-back over the
+//           preceding tiles, and goes out through a shared-memory reorder so that every
+//           bucket run is written contiguously (prefix keys and codes first, then the
+//           full keys through the same shared words);
+//   detect  the neighbour pairs with equal prefixes whose keys are out of order list
+//           their runs (first position and length);
+//   fix-up  one warp sorts each listed run by (key, merged index).
+// Carrying the full keys costs 12 bytes per point and pass; reading them back by code
+// after the passes would cost a random 8-byte read per point, about 64 bytes of DRAM
+// traffic each on this part.  A run longer than kRunMax with keys out of order (a
+// cluster of distinct coordinates narrower than the item's range / 2^32) sets the
+// fallback flag, and the full sort -- the same pass kernel on the 64-bit key, eight
+// digit passes -- runs from the start.  The plans live on the device, so the whole sort
+// is launched without a host round trip (and can be captured in a CUDA graph); kernels
+// of a stage that does not run exit at once.
 //
 // Presorted inputs (Sec. 5's pre-sorted points; its Chebyshev points "sort in much less
 // time"): the histogram pass also checks that every item's sources and targets are each
@@ -24,6 +44,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fgt1d_internal.h"
 #include "kernels.h"
@@ -38,6 +59,51 @@ __device__ __forceinline__ uint64_t coord_key(double c) {
 
 __device__ __forceinline__ bool coord_nonfinite(double c) {
     return ((uint64_t)__double_as_longlong(c) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
+}
+
+// ---- prefix keys ----------------------------------------------------------------------
+// The bits of the coordinate of key k (inverse of coord_key; -0.0 comes back as +0.0).
+__device__ __forceinline__ uint64_t key_bits(uint64_t k) {
+    return (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+}
+
+// Q(z) = sign(z) floor(|z| / 2^(eh - 1075)) from the bits of z: the 53-bit significand
+// (implicit bit included, subnormals at exponent 1) shifted right by eh - e.  It is a
+// non-decreasing function of z for every |z| whose exponent is at most eh.
+__device__ __forceinline__ int64_t fixq(uint64_t b, int eh) {
+    const int ef = (int)((b >> 52) & 0x7FF);
+    uint64_t m = b & 0x000FFFFFFFFFFFFFull;
+    int e = 1;
+    if (ef) {
+        m |= 0x0010000000000000ull;
+        e = ef;
+    }
+    const int sh = eh - e;  // >= 0 inside the item's range
+    const uint64_t q = sh >= 64 ? 0ull : (sh <= 0 ? m : (m >> sh));
+    return (b >> 63) ? -(int64_t)q : (int64_t)q;
+}
+
+// The 32-bit prefix key of key k in an item with map m; padding (all-ones key) and
+// anything outside the map's range go to 0xFFFFFFFF.
+__device__ __forceinline__ uint32_t prefix_of_key(uint64_t k, const PrefixMap& m) {
+    if (k == ~0ull) return 0xFFFFFFFFu;
+    const uint64_t r = (uint64_t)(fixq(key_bits(k), m.eh) - m.qlo) >> m.sh;
+    return r > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)r;
+}
+
+// The map of an item whose keys span [klo, khi] (klo > khi: no points).
+__device__ __forceinline__ PrefixMap make_prefix_map(uint64_t klo, uint64_t khi) {
+    PrefixMap m;
+    m.qlo = 0;
+    m.eh = 1;
+    m.sh = 0;
+    if (klo > khi) return m;
+    const uint64_t blo = key_bits(klo), bhi = key_bits(khi);
+    m.eh = max(1, max((int)((blo >> 52) & 0x7FF), (int)((bhi >> 52) & 0x7FF)));
+    m.qlo = fixq(blo, m.eh);
+    const uint64_t span = (uint64_t)(fixq(bhi, m.eh) - m.qlo);
+    m.sh = span >> 32 ? 32 - __clzll((long long)span) : 0;  // (span >> sh) < 2^32
+    return m;
 }
 
 // ---- item table -----------------------------------------------------------------------
@@ -144,39 +210,120 @@ cudaError_t launch_item_single(int64_t M, int64_t N, double delta, Item* items, 
 // then padding (all-ones key, sorted last).
 __device__ __forceinline__ void merged_point(const SortArgs& a, const Item& it, int64_t g, uint64_t& key,
                                              uint32_t& val, bool& bad) {
+    // the address is chosen by selects and the load is unconditional (padding reads the
+    // item's first point), so that a thread's loads of several points are all in flight
     const int64_t l = g - it.start;
-    if (l < it.nsrc) {
-        const double c = a.y[it.y_off + l];
-        bad |= coord_nonfinite(c);
-        key = coord_key(c);
-        val = (uint32_t)(it.y_off + l);
-    } else if (l < it.nsrc + it.ntgt) {
-        const double c = a.x[it.x_off + (l - it.nsrc)];
-        bad |= coord_nonfinite(c);
-        key = coord_key(c);
-        val = (uint32_t)(a.N + it.x_off + (l - it.nsrc));
-    } else {
-        key = ~0ull;
-        val = 0xFFFFFFFFu;
-    }
+    const bool src = l < it.nsrc, tgt = !src && l < it.nsrc + it.ntgt;
+    const double* p = src ? a.y + it.y_off + l
+                          : (tgt ? a.x + it.x_off + (l - it.nsrc) : (it.nsrc > 0 ? a.y + it.y_off : a.x + it.x_off));
+    const double c = *p;
+    bad |= (src || tgt) && coord_nonfinite(c);
+    key = (src || tgt) ? coord_key(c) : ~0ull;
+    val = src ? (uint32_t)(it.y_off + l) : (tgt ? (uint32_t)(a.N + it.x_off + (l - it.nsrc)) : 0xFFFFFFFFu);
 }
 
-// ---- per-item histograms of all digits ----------------------------------------------------
-// Each block walks a contiguous range of tiles, counting in shared memory and flushing
-// the non-zero counts to the current item's histogram when the item changes.
-__global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
-    __shared__ uint32_t sh[kSortDigits][256];
+// ---- per-item coordinate range (prefix sort) ----------------------------------------------
+// Each block walks a contiguous range of tiles and flushes its extremes when the item
+// changes; the smallest key is kept complemented, so both ends are atomicMax on words
+// that start at zero.
+__global__ void __launch_bounds__(256) k_sort_range(SortArgs a) {
+    __shared__ int s_item;
+    __shared__ uint64_t s_lo[8], s_hi[8];
+    const int64_t T = *a.total_tiles;
+    const int64_t per = (T + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long* range = reinterpret_cast<unsigned long long*>(a.maps);
+    uint64_t lo = ~0ull, hi = 0ull;
+    int cur = -1;
+    auto flush = [&](int item) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            lo = min(lo, (uint64_t)__shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, (uint64_t)__shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            s_lo[w] = lo;
+            s_hi[w] = hi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t l = s_lo[0], h = s_hi[0];
+            for (int q = 1; q < 8; ++q) {
+                l = min(l, s_lo[q]);
+                h = max(h, s_hi[q]);
+            }
+            if (l <= h) {
+                atomicMax(&range[2 * item], (unsigned long long)~l);
+                atomicMax(&range[2 * item + 1], (unsigned long long)h);
+            }
+        }
+        __syncthreads();
+        lo = ~0ull;
+        hi = 0ull;
+    };
+    for (int64_t t = t0; t < t1; ++t) {
+        if (threadIdx.x == 0) s_item = item_of_tile(a.items, a.B, t);
+        __syncthreads();
+        const int item = s_item;
+        if (item != cur) {
+            if (cur >= 0) flush(cur);
+            cur = item;
+        }
+        const Item it = a.items[item];
+        double c[kSortIPT];
+        bool real[kSortIPT];
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {  // all loads first
+            const int64_t l = t * kTile + threadIdx.x + j * 256 - it.start;
+            real[j] = l < it.nsrc + it.ntgt;
+            c[j] = *(l < it.nsrc ? a.y + it.y_off + l
+                                 : (real[j] ? a.x + it.x_off + (l - it.nsrc) : (it.nsrc > 0 ? a.y + it.y_off : a.x + it.x_off)));
+        }
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j)
+            if (real[j]) {
+                const uint64_t k = coord_key(c[j]);
+                lo = min(lo, k);
+                hi = max(hi, k);
+            }
+        __syncthreads();  // s_item is rewritten for the next tile
+    }
+    if (cur >= 0) flush(cur);
+}
+
+// The per-item prefix maps, in place of the ranges (one thread per item).
+__global__ void k_prefix_maps(SortArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.B) return;
+    const uint64_t* range = reinterpret_cast<const uint64_t*>(a.maps);
+    const uint64_t klo = ~range[2 * b], khi = range[2 * b + 1];
+    a.maps[b] = make_prefix_map(klo, khi);
+}
+
+// ---- per-item digit histograms ------------------------------------------------------------
+// PREFIX: the four digits of the prefix keys, and the presorted check; the prefix keys
+// and the merged codes are written out for the first digit pass.  Otherwise (the
+// full sort, only after a fallback): the eight digits of the 64-bit keys.  Each block
+// walks a contiguous range of tiles, counting in shared memory and flushing the non-zero
+// counts to the current item's histogram when the item changes.
+template <bool PREFIX>
+__global__ void __launch_bounds__(256, 4) k_sort_hist(SortArgs a) {
+    constexpr int ND = PREFIX ? kPrefixDigits : kSortDigits;
+    if (!PREFIX && (!a.pplan->fallback || (*a.status & kStatusSortTimeout))) return;
+    __shared__ uint32_t sh[ND][256];
     __shared__ int s_item;
     const int64_t T = *a.total_tiles;
     const int64_t per = (T + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
-    for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < ND * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
     int cur = -1;
     bool bad = false;
     auto flush = [&](int item) {
         __syncthreads();
         uint32_t* h = a.hist + (size_t)item * kSortDigits * 256;
-        for (int i = threadIdx.x; i < kSortDigits * 256; i += blockDim.x) {
+        for (int i = threadIdx.x; i < ND * 256; i += blockDim.x) {
             const uint32_t v = (&sh[0][0])[i];
             if (v) {
                 atomicAdd(&h[i], v);
@@ -195,29 +342,39 @@ __global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
             cur = item;
         }
         const Item it = a.items[item];
-        uint32_t last[kSortDigits], run[kSortDigits];
+        PrefixMap m;
+        if (PREFIX) m = a.maps[item];
+        uint32_t last[ND], run[ND];
 #pragma unroll
-        for (int d = 0; d < kSortDigits; ++d) { last[d] = 0; run[d] = 0; }
-        for (int e = threadIdx.x; e < kTile; e += blockDim.x) {
-            // presorted check: the key before this one in the same run (sources or
-            // targets of this item), from the lane below or, for lane 0, from memory (that
-            // load is issued next to the point's own)
-            const int64_t l = t * kTile + e - it.start;
-            const bool chk = l > 0 && l != it.nsrc && l < it.nsrc + it.ntgt;
-            double cprev = 0.0;
-            if (chk && (threadIdx.x & 31) == 0)
-                cprev = l < it.nsrc ? a.y[it.y_off + l - 1] : a.x[it.x_off + (l - it.nsrc) - 1];
+        for (int d = 0; d < ND; ++d) {
+            last[d] = 0;
+            run[d] = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            const int64_t g = t * kTile + threadIdx.x + j * 256;
             uint64_t k;
             uint32_t v;
-            merged_point(a, it, t * kTile + e, k, v, bad);
-            uint64_t kp = __shfl_up_sync(0xffffffffu, k, 1);
-            if (chk) {
-                if ((threadIdx.x & 31) == 0) kp = coord_key(cprev);
-                unsorted |= kp > k;
+            merged_point(a, it, g, k, v, bad);
+            uint64_t dk = k;
+            if (PREFIX) {
+                // the first digit pass reads buffer 1: codes, full keys and prefix keys
+                a.valsB[g] = v;
+                a.keysB[g] = k;
+                dk = prefix_of_key(k, m);
+                a.pre[a.Ppad + g] = (uint32_t)dk;
+                // presorted check: the key before this point in the same run (sources or
+                // targets of this item), from the lane below or, for lane 0, from memory
+                const int64_t l = g - it.start;
+                const bool chk = l > 0 && l != it.nsrc && l < it.nsrc + it.ntgt;
+                uint64_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+                if (lane == 0 && chk)
+                    kp = coord_key(l < it.nsrc ? a.y[it.y_off + l - 1] : a.x[it.x_off + (l - it.nsrc) - 1]);
+                if (chk) unsorted |= kp > k;
             }
 #pragma unroll
-            for (int d = 0; d < kSortDigits; ++d) {
-                const uint32_t dg = (uint32_t)(k >> (8 * d)) & 255u;
+            for (int d = 0; d < ND; ++d) {
+                const uint32_t dg = (uint32_t)(dk >> (8 * d)) & 255u;
                 if (dg != last[d]) {
                     if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
                     last[d] = dg;
@@ -227,23 +384,29 @@ __global__ void __launch_bounds__(256) k_sort_hist(SortArgs a) {
             }
         }
 #pragma unroll
-        for (int d = 0; d < kSortDigits; ++d)
+        for (int d = 0; d < ND; ++d)
             if (run[d]) atomicAdd(&sh[d][last[d]], run[d]);
         __syncthreads();
     }
     if (cur >= 0) flush(cur);
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, kStatusNonFinite);
-    if (__any_sync(0xffffffffu, unsorted) && (threadIdx.x & 31) == 0) atomicOr(&a.plan->unsorted, 1u);
+    if (PREFIX) {
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, kStatusNonFinite);
+        if (__any_sync(0xffffffffu, unsorted) && lane == 0) atomicOr(&a.plan->unsorted, 1u);
+    }
 }
 
 // ---- per-item bucket starts and the digits that need a pass (one block per item) ----------
+template <bool PREFIX>
 __global__ void __launch_bounds__(256) k_sort_plan(SortArgs a) {
+    constexpr int ND = PREFIX ? kPrefixDigits : kSortDigits;
+    if (!PREFIX && (!a.pplan->fallback || (*a.status & kStatusSortTimeout))) return;
     __shared__ uint32_t scan[256];
+    uint32_t* mask = PREFIX ? &a.pplan->mask : &a.plan->active_mask;
     const int b = blockIdx.x;
     const Item it = a.items[b];
     const int t = threadIdx.x;
     const int64_t Pb = it.ntiles * kTile;
-    for (int d = 0; d < kSortDigits; ++d) {
+    for (int d = 0; d < ND; ++d) {
         const uint32_t v = a.hist[((size_t)b * kSortDigits + d) * 256 + t];
         scan[t] = v;
         __syncthreads();
@@ -255,24 +418,48 @@ __global__ void __launch_bounds__(256) k_sort_plan(SortArgs a) {
         }
         a.offs[((size_t)b * kSortDigits + d) * 256 + t] = (uint32_t)it.start + scan[t] - v;
         const int partial = (v != 0 && (int64_t)v != Pb);
-        if (__syncthreads_or(partial) && t == 0) atomicOr(&a.plan->active_mask, 1u << d);
+        if (__syncthreads_or(partial) && t == 0) atomicOr(mask, 1u << d);
     }
 }
 
-// ---- the pass chain: which buffers each active digit reads and writes -------------------
-__global__ void k_sort_chain(SortPlan* plan) {
-    const uint32_t mask = plan->active_mask;
-    int cur = -1, n_active = 0;
+// ---- the pass chains: which buffers each active digit reads and writes -------------------
+// Prefix sort (or the merge of presorted runs): the histogram pass left the prefix keys
+// and codes in buffer 1; the active digits ping-pong from there.
+__global__ void k_sort_chain(SortArgs a) {
+    SortPlan* plan = a.plan;
+    PrefixPlan* pp = a.pplan;
     for (int d = 0; d < kSortDigits; ++d) {
         plan->active[d] = 0;
         plan->src[d] = 0;
         plan->dst[d] = 0;
     }
-    plan->merge = plan->unsorted ? 0u : 1u;
-    if (plan->merge) {  // presorted runs: no digit pass, k_sort_merge writes buffer A
-        plan->final_buf = 0;
-        return;
+    for (int d = 0; d < kPrefixDigits; ++d) {
+        pp->active[d] = 0;
+        pp->src[d] = 0;
+        pp->dst[d] = 0;
     }
+    plan->final_buf = 0;  // (the merge writes buffer A)
+    plan->merge = plan->unsorted ? 0u : 1u;
+    int cur = 1;
+    if (!plan->merge)  // (presorted runs: no digit pass, k_sort_merge writes buffer A)
+        for (int d = 0; d < kPrefixDigits; ++d) {
+            if (!((pp->mask >> d) & 1u)) continue;  // one populated bucket: the order stands
+            pp->active[d] = 1;
+            pp->src[d] = cur;
+            pp->dst[d] = 1 - cur;
+            cur = 1 - cur;
+        }
+    pp->final_buf = cur;
+    if (!plan->merge) plan->final_buf = cur;
+}
+
+// Full sort (after a fallback): digits with more than one populated bucket, ping-pong
+// between buffers A and B.
+__global__ void k_sort_chain_full(SortArgs a) {
+    if (!a.pplan->fallback || (*a.status & kStatusSortTimeout)) return;
+    SortPlan* plan = a.plan;
+    const uint32_t mask = plan->active_mask;
+    int cur = -1, n_active = 0;
     for (int d = 0; d < kSortDigits; ++d) {
         if (!((mask >> d) & 1u)) continue;
         plan->active[d] = 1;
@@ -309,176 +496,391 @@ __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
 constexpr uint64_t kDescAgg = 1ull << 62;
 constexpr uint64_t kDescInc = 2ull << 62;
 
+template <typename K>
 struct SortSmem {
-    uint64_t keys[kSortTile];
-    uint32_t vals[kSortTile];
+    // the sorted tile: keys and codes; the prefix passes stage their full keys in the
+    // same words afterwards
+    union {
+        struct {
+            K keys[kSortTile];
+            uint32_t vals[kSortTile];
+        } kv;
+        uint64_t full[kSortTile];
+    } t;
     uint32_t wcnt[kSortThreads / 32][256];
     uint32_t tile_start[256];
     uint32_t gbase[256];
+    uint32_t wsum[kSortThreads / 32];
     uint32_t tile_id;
+    int item;
 };
 
+// PREFIX: a pass of the prefix sort: 32-bit prefix keys, with the codes and the full
+// 64-bit keys as payload (buffers: 0 = (pre, keysA, valsA), 1 = (pre + Ppad, keysB,
+// valsB)).  Otherwise a pass of the full sort (64-bit keys and codes, buffers A and B),
+// which runs only after a fallback.  Every block takes tiles in order from the pass's
+// counter until none is left, so a grid of any size is correct: the look-back only
+// waits on tiles that running blocks hold.
+template <bool PREFIX>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d) {
-    const SortPlan* pl = a.plan;
-    if (!pl->active[d]) return;
+    using K = typename std::conditional<PREFIX, uint32_t, uint64_t>::type;
+    int src, dst;
+    uint32_t* ctr;
+    if (PREFIX) {
+        if (!a.pplan->active[d]) return;
+        src = a.pplan->src[d];
+        dst = a.pplan->dst[d];
+        ctr = &a.pplan->pass_ctr[d];
+    } else {
+        if (!a.pplan->fallback || (*a.status & kStatusSortTimeout) || !a.plan->active[d]) return;
+        src = a.plan->src[d];
+        dst = a.plan->dst[d];
+        ctr = &a.tile_ctr[d];
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
-    __shared__ int s_item;
-    const int src = pl->src[d], dst = pl->dst[d];
-    const uint64_t* __restrict__ kin = src == 1 ? a.keysB : a.keysA;
+    SortSmem<K>& sm = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    // sort keys
+    K* kb0 = PREFIX ? reinterpret_cast<K*>(a.pre) : reinterpret_cast<K*>(a.keysA);
+    K* kb1 = PREFIX ? reinterpret_cast<K*>(a.pre + a.Ppad) : reinterpret_cast<K*>(a.keysB);
+    const K* __restrict__ kin = src == 1 ? kb1 : kb0;
+    K* __restrict__ kout = dst == 1 ? kb1 : kb0;
     const uint32_t* __restrict__ vin = src == 1 ? a.valsB : a.valsA;
-    uint64_t* __restrict__ kout = dst == 1 ? a.keysB : a.keysA;
     uint32_t* __restrict__ vout = dst == 1 ? a.valsB : a.valsA;
+    // full-key payload of the prefix passes
+    const uint64_t* __restrict__ fin = src == 1 ? a.keysB : a.keysA;
+    uint64_t* __restrict__ fout = dst == 1 ? a.keysB : a.keysA;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int shift = 8 * d;
+    const int64_t T = *a.total_tiles;
+    uint64_t* desc = a.desc + (size_t)d * a.desc_stride;
 
-    if (tid == 0) {
-        sm.tile_id = atomicAdd(&a.tile_ctr[d], 1u);
-        s_item = (int64_t)sm.tile_id < *a.total_tiles ? item_of_tile(a.items, a.B, sm.tile_id) : -1;
-    }
-    for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&sm.wcnt[0][0])[i] = 0;
-    __syncthreads();
-    if (s_item < 0) return;
-    const uint32_t tile = sm.tile_id;
-    const Item it = a.items[s_item];
-    const int64_t base = (int64_t)tile * kSortTile;
-    const uint32_t* __restrict__ item_offs = a.offs + ((size_t)s_item * kSortDigits + d) * 256;
+    for (;;) {
+        if (tid == 0) {
+            sm.tile_id = atomicAdd(ctr, 1u);
+            sm.item = (int64_t)sm.tile_id < T ? item_of_tile(a.items, a.B, sm.tile_id) : -1;
+        }
+        for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&sm.wcnt[0][0])[i] = 0;
+        __syncthreads();
+        if (sm.item < 0) return;
+        const uint32_t tile = sm.tile_id;
+        const int item = sm.item;
+        const Item it = a.items[item];
+        const int64_t base = (int64_t)tile * kSortTile;
+        const uint32_t* __restrict__ item_offs = a.offs + ((size_t)item * kSortDigits + d) * 256;
 
-    // load (warp-striped: warp w owns items [w*32*IPT, (w+1)*32*IPT), slot j covers 32 consecutive items)
-    uint64_t key[kSortIPT];
-    uint32_t val[kSortIPT];
-    uint32_t rank[kSortIPT];
-    bool bad = false;
+        // load (warp-striped: warp w owns keys [w*32*IPT, (w+1)*32*IPT), slot j covers 32 consecutive keys)
+        K key[kSortIPT];
+        uint32_t val[kSortIPT];
+        uint32_t rank[kSortIPT];
+        bool bad = false;
+        if (!PREFIX && src < 0) {  // (the prefix passes start from the histogram pass's output)
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
-        const int li = w * 32 * kSortIPT + j * 32 + lane;
-        const int64_t g = base + li;
-        if (src < 0) {
-            merged_point(a, it, g, key[j], val[j], bad);
+            for (int j = 0; j < kSortIPT; ++j) {
+                uint64_t k;
+                merged_point(a, it, base + w * 32 * kSortIPT + j * 32 + lane, k, val[j], bad);
+                key[j] = (K)k;
+            }
         } else {
-            key[j] = kin[g];
-            val[j] = vin[g];
+#pragma unroll
+            for (int j = 0; j < kSortIPT; ++j) {
+                const int64_t g = base + w * 32 * kSortIPT + j * 32 + lane;
+                key[j] = kin[g];
+                if (!PREFIX) val[j] = vin[g];
+            }
         }
-    }
-    // stable warp ranking per slot: the lanes holding the same digit are found with
-    // eight ballots (one per digit bit), for all slots first (independent work); then,
-    // slot by slot, every lane reads the warp's running count for its digit and the
-    // lowest peer adds the slot's count
-    unsigned peers[kSortIPT];
+        // stable warp ranking per slot: the lanes holding the same digit are found with
+        // eight ballots (one per digit bit), for all slots first (independent work); then,
+        // slot by slot, every lane reads the warp's running count for its digit and the
+        // lowest peer adds the slot's count
+        unsigned peers[kSortIPT];
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
-        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        unsigned pm = 0xffffffffu;
+        for (int j = 0; j < kSortIPT; ++j) {
+            const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+            unsigned pm = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned m = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
-            pm &= ((dg >> b) & 1u) ? m : ~m;
+            for (int b = 0; b < 8; ++b) {
+                const unsigned mb = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+                pm &= ((dg >> b) & 1u) ? mb : ~mb;
+            }
+            peers[j] = pm;
         }
-        peers[j] = pm;
-    }
-    const unsigned lt = lanemask_lt();
+        const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
-        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        const uint32_t old = sm.wcnt[w][dg];
-        __syncwarp();
-        rank[j] = old + __popc(peers[j] & lt);
-        if ((peers[j] & lt) == 0) sm.wcnt[w][dg] = old + __popc(peers[j]);
-        __syncwarp();
-    }
-    __syncthreads();
-    // per digit: exclusive prefix over warps, tile count
-    uint32_t tot = 0;
-    {
-        const int dg = tid;  // kSortThreads == 256 digits
-#pragma unroll
-        for (int ww = 0; ww < kSortThreads / 32; ++ww) {
-            uint32_t c = sm.wcnt[ww][dg];
-            sm.wcnt[ww][dg] = tot;
-            tot += c;
+        for (int j = 0; j < kSortIPT; ++j) {
+            const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+            const uint32_t old = sm.wcnt[w][dg];
+            __syncwarp();
+            rank[j] = old + __popc(peers[j] & lt);
+            if ((peers[j] & lt) == 0) sm.wcnt[w][dg] = old + __popc(peers[j]);
+            __syncwarp();
         }
-        sm.tile_start[dg] = tot;
-    }
-    __syncthreads();
-    // exclusive scan of tile counts over digits -> tile_start
-    {
-        uint32_t v = sm.tile_start[tid];
-        uint32_t inc = v;
+        // the prefix passes' codes, loaded now: their latency runs under the scans and
+        // the look-back
+        if (PREFIX) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
+            for (int j = 0; j < kSortIPT; ++j) val[j] = vin[base + w * 32 * kSortIPT + j * 32 + lane];
         }
-        __shared__ uint32_t wsum[kSortThreads / 32];
-        if (lane == 31) wsum[w] = inc;
         __syncthreads();
-        uint32_t wpre = 0;
-        for (int ww = 0; ww < w; ++ww) wpre += wsum[ww];
-        __syncthreads();
-        sm.tile_start[tid] = wpre + inc - v;
-    }
-    // decoupled look-back over the item's earlier tiles for this digit's global base;
-    // each round issues the loads of kLookAhead predecessors at once
-    {
-        constexpr int kLookAhead = 8;
-        const int dg = tid;
-        uint64_t* desc = a.desc + (size_t)d * a.desc_stride;
-        uint32_t excl = 0;
-        if ((int64_t)tile == it.tile0) {
-            st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)tot);
-        } else {
-            st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescAgg | (uint64_t)tot);
-            int64_t j = (int64_t)tile - 1;
-            bool done = false;
-            while (!done) {
-                uint64_t v[kLookAhead];
+        // per digit: exclusive prefix over warps, tile count
+        uint32_t tot = 0;
+        {
+            const int dg = tid;  // kSortThreads == 256 digits
 #pragma unroll
-                for (int q = 0; q < kLookAhead; ++q)
-                    v[q] = (j - q >= it.tile0) ? ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg]) : kDescInc;
+            for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+                const uint32_t c = sm.wcnt[ww][dg];
+                sm.wcnt[ww][dg] = tot;
+                tot += c;
+            }
+        }
+        // exclusive scan of tile counts over digits -> tile_start
+        {
+            uint32_t inc = tot;
 #pragma unroll
-                for (int q = 0; q < kLookAhead; ++q) {
-                    if (done) break;
-                    uint64_t x = v[q];
-                    if ((x >> 62) == 0) {
-                        const long long t0 = clock64();
-                        while (((x = ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg])) >> 62) == 0) {
-                            if (clock64() - t0 > a.spin_limit) {
-                                atomicOr(a.status, kStatusTimeout | kStatusSortTimeout);
-                                x = kDescInc;
-                                break;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (lane == 31) sm.wsum[w] = inc;
+            __syncthreads();
+            uint32_t wpre = 0;
+            for (int ww = 0; ww < w; ++ww) wpre += sm.wsum[ww];
+            sm.tile_start[tid] = wpre + inc - tot;
+        }
+        // decoupled look-back over the item's earlier tiles for this digit's global base;
+        // each round issues the loads of kLookAhead predecessors at once
+        {
+            constexpr int kLookAhead = 8;
+            const int dg = tid;
+            uint32_t excl = 0;
+            if ((int64_t)tile == it.tile0) {
+                st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)tot);
+            } else {
+                st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescAgg | (uint64_t)tot);
+                int64_t j = (int64_t)tile - 1;
+                bool done = false;
+                while (!done) {
+                    uint64_t v[kLookAhead];
+#pragma unroll
+                    for (int q = 0; q < kLookAhead; ++q)
+                        v[q] = (j - q >= it.tile0) ? ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg]) : kDescInc;
+#pragma unroll
+                    for (int q = 0; q < kLookAhead; ++q) {
+                        if (done) break;
+                        uint64_t x = v[q];
+                        if ((x >> 62) == 0) {
+                            const long long t0 = clock64();
+                            while (((x = ld_volatile_u64(&desc[(size_t)(j - q) * 256 + dg])) >> 62) == 0) {
+                                if (clock64() - t0 > a.spin_limit) {
+                                    atomicOr(a.status, kStatusTimeout | kStatusSortTimeout);
+                                    x = kDescInc;
+                                    break;
+                                }
                             }
                         }
+                        excl += (uint32_t)(x & 0xFFFFFFFFull);
+                        if ((x >> 62) == 2) done = true;
                     }
-                    excl += (uint32_t)(x & 0xFFFFFFFFull);
-                    if ((x >> 62) == 2) done = true;
+                    j -= kLookAhead;
                 }
-                j -= kLookAhead;
+                st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)(excl + tot));
             }
-            st_volatile_u64(&desc[(size_t)tile * 256 + dg], kDescInc | (uint64_t)(excl + tot));
+            sm.gbase[dg] = item_offs[dg] + excl;
         }
-        sm.gbase[dg] = item_offs[dg] + excl;
-    }
-    __syncthreads();
-    // reorder through shared memory
+        __syncthreads();
+        // reorder through shared memory: rank[j] becomes the position in the sorted tile
 #pragma unroll
-    for (int j = 0; j < kSortIPT; ++j) {
-        const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
-        const uint32_t pos = sm.tile_start[dg] + sm.wcnt[w][dg] + rank[j];
-        sm.keys[pos] = key[j];
-        sm.vals[pos] = val[j];
+        for (int j = 0; j < kSortIPT; ++j) {
+            const uint32_t dg = (uint32_t)(key[j] >> shift) & 255u;
+            rank[j] += sm.tile_start[dg] + sm.wcnt[w][dg];
+            sm.t.kv.keys[rank[j]] = key[j];
+            sm.t.kv.vals[rank[j]] = val[j];
+        }
+        __syncthreads();
+        const int64_t item_end = it.start + it.ntiles * kTile;
+        uint32_t out[kSortIPT];  // output position of sorted-tile position tid + j * kSortThreads
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            const int i = tid + j * kSortThreads;
+            const K k = sm.t.kv.keys[i];
+            const uint32_t dg = (uint32_t)(k >> shift) & 255u;
+            out[j] = sm.gbase[dg] + (uint32_t)i - sm.tile_start[dg];
+            if ((int64_t)out[j] < item_end) {  // always true unless a look-back wait timed out
+                kout[out[j]] = k;
+                vout[out[j]] = sm.t.kv.vals[i];
+            }
+        }
+        if (PREFIX) {  // the full keys, through the same shared words
+            uint64_t full[kSortIPT];
+#pragma unroll
+            for (int j = 0; j < kSortIPT; ++j) full[j] = fin[base + w * 32 * kSortIPT + j * 32 + lane];
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kSortIPT; ++j) sm.t.full[rank[j]] = full[j];
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kSortIPT; ++j)
+                if ((int64_t)out[j] < item_end) fout[out[j]] = sm.t.full[tid + j * kSortThreads];
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, kStatusNonFinite);
+        __syncthreads();  // the shared tile is reused by the next tile
     }
-    __syncthreads();
-    const int64_t item_end = it.start + it.ntiles * kTile;
-    for (int i = tid; i < kSortTile; i += kSortThreads) {
-        const uint64_t k = sm.keys[i];
-        const uint32_t dg = (uint32_t)(k >> shift) & 255u;
-        const int64_t o = (int64_t)sm.gbase[dg] + i - sm.tile_start[dg];
-        if (o < item_end) {  // always true unless a look-back wait timed out
-            kout[o] = k;
-            vout[o] = sm.vals[i];
+}
+
+
+// ---- the full keys, and runs of equal prefix keys ------------------------------------------
+// Lists run [s, s + len) for the fix-up.
+__device__ __forceinline__ void push_run(const SortArgs& a, uint64_t* runs, int64_t s, int len) {
+    const uint32_t idx = atomicAdd(&a.pplan->nruns, 1u);
+    if ((int64_t)idx < a.Ppad / 2) runs[idx] = (uint64_t)s | ((uint64_t)len << 40);
+    else atomicOr(&a.pplan->fallback, 1u);
+}
+
+// A run that starts at s inside a thread's window and reaches past it, its first len
+// points seen up to pos (exclusive; last key kprev, descent flag d): walks on while the
+// run lasts and lists it if it holds a descent.  A run longer than kRunMax is not
+// listed: the length check of its descents (check_extent) sends the sort to the fallback.
+__device__ __noinline__ void walk_run(const SortArgs& a, const uint32_t* pre, const uint64_t* keys, uint64_t* runs,
+                                      int64_t end, int64_t s, int64_t pos, uint32_t pk, uint64_t kprev, int len,
+                                      bool d) {
+    while (pos < end && pre[pos] == pk) {
+        if (len >= kRunMax) return;
+        const uint64_t kk = keys[pos];
+        d |= kprev > kk;
+        kprev = kk;
+        ++len;
+        ++pos;
+    }
+    if (d) push_run(a, runs, s, len);
+}
+
+// A descent in a run of prefix pk that holds points [lo, hi) and may extend below lo
+// (down) or from hi on (up): sets the fallback flag when the run is longer than kRunMax.
+__device__ __noinline__ void check_extent(const SortArgs& a, const uint32_t* pre, int64_t start, int64_t end,
+                                          int64_t lo, int64_t hi, uint32_t pk, bool down, bool up) {
+    while (down && lo > start && pre[lo - 1] == pk && hi - lo <= kRunMax) --lo;
+    while (up && hi < end && pre[hi] == pk && hi - lo <= kRunMax) ++hi;
+    if (hi - lo > kRunMax) atomicOr(&a.pplan->fallback, 1u);
+}
+
+// One block per tile (grid-stride), each thread 16 consecutive positions of the sorted
+// prefix keys and full keys: the window's neighbour pairs with equal prefixes (bit mask
+// eqm) and, among them, keys out of order (a descent, mask dsm).  A run that starts in
+// the window is listed when it holds a descent, and followed past the window by
+// walk_run when it reaches beyond it; a descent in a run that reaches outside the
+// window also has its run's length checked.  Neither walk happens for runs inside one
+// window, which are nearly all of them.
+__global__ void __launch_bounds__(256) k_sort_detect(SortArgs a) {
+    if (a.plan->merge || (*a.status & kStatusSortTimeout)) return;
+    __shared__ int s_item;
+    const int fb = a.pplan->final_buf;
+    const uint32_t* pre = a.pre + (fb ? a.Ppad : 0);
+    const uint64_t* keys = fb ? a.keysB : a.keysA;
+    uint64_t* runs = reinterpret_cast<uint64_t*>(a.pre + (fb ? 0 : a.Ppad));
+    const int64_t T = *a.total_tiles;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        if (threadIdx.x == 0) s_item = item_of_tile(a.items, a.B, t);
+        __syncthreads();
+        const Item it = a.items[s_item];
+        const int64_t start = it.start, end = it.start + it.nsrc + it.ntgt;
+        const int64_t g0 = t * kTile + threadIdx.x * kSortIPT;  // a multiple of 16
+        uint32_t p[kSortIPT];
+        uint64_t k[kSortIPT];
+#pragma unroll
+        for (int q = 0; q < kSortIPT / 4; ++q) {
+            const uint4 pp = reinterpret_cast<const uint4*>(pre + g0)[q];
+            p[4 * q] = pp.x, p[4 * q + 1] = pp.y, p[4 * q + 2] = pp.z, p[4 * q + 3] = pp.w;
+        }
+#pragma unroll
+        for (int q = 0; q < kSortIPT / 2; ++q) {
+            const ulonglong2 kk = reinterpret_cast<const ulonglong2*>(keys + g0)[q];
+            k[2 * q] = kk.x, k[2 * q + 1] = kk.y;
+        }
+        if (g0 + 1 < end) {
+            const uint32_t p16 = g0 + kSortIPT < end ? pre[g0 + kSortIPT] : ~p[kSortIPT - 1];
+            uint32_t eqm = 0, dsm = 0;
+#pragma unroll
+            for (int q = 0; q < kSortIPT; ++q) {
+                const uint32_t pn = q + 1 < kSortIPT ? p[q + 1] : p16;
+                const bool e = g0 + q + 1 < end && p[q] == pn;
+                eqm |= (uint32_t)e << q;
+                if (q + 1 < kSortIPT && e && k[q] > k[q + 1]) dsm |= 1u << q;
+            }
+            if (eqm) {
+                uint64_t k16 = 0;
+                if ((eqm >> 15) & 1u) {
+                    k16 = keys[g0 + kSortIPT];
+                    if (k[kSortIPT - 1] > k16) dsm |= 1u << 15;
+                }
+                const bool before = g0 > start && pre[g0 - 1] == p[0];  // the first run began earlier
+                // runs that start in the window
+                uint32_t st = eqm & ~((eqm << 1) | (before ? 1u : 0u));
+                while (st) {
+                    const int q = __ffs(st) - 1;
+                    st &= st - 1;
+                    const int j = __ffs(~(eqm >> q)) - 1;  // equal pairs from q: points q .. q + j
+                    const bool d = (dsm & (((1u << j) - 1u) << q)) != 0;
+                    if (q + j == kSortIPT) walk_run(a, pre, keys, runs, end, g0 + q, g0 + kSortIPT + 1, p[q], k16, j + 1, d);
+                    else if (d) push_run(a, runs, g0 + q, j + 1);
+                }
+                // descents in runs that reach outside the window
+                const int j0 = __ffs(~eqm) - 1;  // equal pairs from point 0
+                const uint32_t first = before ? (1u << j0) - 1u : 0u;
+                if (dsm & first) check_extent(a, pre, start, end, g0, g0 + j0 + 1, p[0], true, j0 == kSortIPT);
+                if ((eqm >> 15) & 1u && !(before && j0 == kSortIPT)) {
+                    const int tl = __clz(~(eqm << 16));  // equal pairs that end at pair 15
+                    if (dsm & (((1u << tl) - 1u) << (kSortIPT - tl)))
+                        check_extent(a, pre, start, end, g0 + kSortIPT - tl, g0 + kSortIPT + 1, p[kSortIPT - 1], false,
+                                     true);
+                }
+            }
+        }
+        __syncthreads();  // s_item is rewritten for the next tile
+    }
+}
+
+// One warp per listed run: each lane takes one point, ranks it by (key, code) among the
+// run's points, and writes it back in place (the final buffer of the prefix sort).
+__global__ void __launch_bounds__(256) k_sort_fixup(SortArgs a) {
+    if (a.plan->merge || a.pplan->fallback || (*a.status & kStatusSortTimeout)) return;
+    const int fb = a.pplan->final_buf;
+    uint64_t* keys = fb ? a.keysB : a.keysA;
+    uint32_t* vals = fb ? a.valsB : a.valsA;
+    const uint64_t* runs = reinterpret_cast<const uint64_t*>(a.pre + (fb ? 0 : a.Ppad));
+    const uint32_t n = (uint32_t)min((int64_t)a.pplan->nruns, a.Ppad / 2);
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
+        const uint64_t e = runs[r];
+        const int64_t s = (int64_t)(e & ((1ull << 40) - 1));
+        const int len = (int)(e >> 40);
+        uint64_t k = ~0ull;
+        uint32_t v = 0xFFFFFFFFu;
+        if (lane < len) {
+            k = keys[s + lane];
+            v = vals[s + lane];
+        }
+        int rank = 0;
+        for (int j = 0; j < len; ++j) {
+            const uint64_t kj = __shfl_sync(0xffffffffu, k, j);
+            const uint32_t vj = __shfl_sync(0xffffffffu, v, j);
+            rank += (kj < k || (kj == k && vj < v)) ? 1 : 0;
+        }
+        __syncwarp();
+        if (lane < len) {
+            keys[s + rank] = k;
+            vals[s + rank] = v;
         }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, kStatusNonFinite);
+}
+
+// Before the full sort of a fallback: clear the look-back words of the prefix digits
+// and the histograms.
+__global__ void __launch_bounds__(256) k_sort_fb_prepare(SortArgs a) {
+    if (!a.pplan->fallback || (*a.status & kStatusSortTimeout)) return;
+    const size_t nd = (size_t)kPrefixDigits * a.desc_stride, nh = (size_t)a.B * kSortDigits * 256;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += stride) a.desc[i] = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += stride) a.hist[i] = 0;
 }
 
 // ---- presorted runs: one merge -------------------------------------------------------
@@ -585,22 +987,41 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_merge(SortArgs a) {
     }
 }
 
-size_t sort_pass_smem() { return sizeof(SortSmem); }
-
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
     if (a.max_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(SortSmem));
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem32 = (int)sizeof(SortSmem<uint32_t>), smem64 = (int)sizeof(SortSmem<uint64_t>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sort_pass<false>, kSortThreads, smem64);
     if (e != cudaSuccess) return e;
-    const int hist_blocks = (int)std::min<int64_t>(a.max_tiles, 152 * 4);
-    k_sort_hist<<<hist_blocks, 256, 0, st>>>(a);
-    k_sort_plan<<<a.B, 256, 0, st>>>(a);
-    k_sort_chain<<<1, 1, 0, st>>>(a.plan);
-    for (int d = 0; d < kSortDigits; ++d)
-        k_sort_pass<<<(unsigned)a.max_tiles, kSortThreads, sizeof(SortSmem), st>>>(a, d);
-    e = cudaFuncSetAttribute(k_sort_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
-    if (e != cudaSuccess) return e;
-    k_sort_merge<<<(unsigned)a.max_tiles, kSortThreads, sizeof(MergeSmem), st>>>(a);
+    const int64_t tiles = a.max_tiles;
+    const int hist_blocks = (int)std::min<int64_t>(tiles, (int64_t)sms * 4);
+    // prefix sort (or the merge of presorted runs)
+    k_sort_range<<<hist_blocks, 256, 0, st>>>(a);
+    k_prefix_maps<<<(a.B + 255) / 256, 256, 0, st>>>(a);
+    k_sort_hist<true><<<hist_blocks, 256, 0, st>>>(a);
+    k_sort_plan<true><<<a.B, 256, 0, st>>>(a);
+    k_sort_chain<<<1, 1, 0, st>>>(a);
+    for (int d = 0; d < kPrefixDigits; ++d) k_sort_pass<true><<<(unsigned)tiles, kSortThreads, smem32, st>>>(a, d);
+    k_sort_merge<<<(unsigned)tiles, kSortThreads, sizeof(MergeSmem), st>>>(a);
+    k_sort_detect<<<(unsigned)std::min<int64_t>(tiles, (int64_t)sms * 8), 256, 0, st>>>(a);
+    k_sort_fixup<<<sms * 4, 256, 0, st>>>(a);
+    // full sort after a fallback: grids of resident size, so that their blocks exit at
+    // once when there is none
+    k_sort_fb_prepare<<<sms * 4, 256, 0, st>>>(a);
+    k_sort_hist<false><<<hist_blocks, 256, 0, st>>>(a);
+    k_sort_plan<false><<<a.B, 256, 0, st>>>(a);
+    k_sort_chain_full<<<1, 1, 0, st>>>(a);
+    const int full_grid = (int)std::min<int64_t>(tiles, (int64_t)std::max(occ, 1) * sms);
+    for (int d = 0; d < kSortDigits; ++d) k_sort_pass<false><<<full_grid, kSortThreads, smem64, st>>>(a, d);
     return cudaGetLastError();
 }
 

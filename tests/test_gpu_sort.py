@@ -74,3 +74,54 @@ def test_perm_almost_presorted(cuda, where):
     else:
         y = np.random.default_rng(12).random(4096)
     assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+
+
+def _binned(n_bins, per_bin, seed, n_free=0):
+    """Points that share 32-bit prefix keys: the range is pinned to [0, 1] (a source at
+    each end), so a prefix is floor(z 2^31); each of n_bins random bins gets per_bin
+    distinct coordinates inside it, dealt at random to targets and sources, plus n_free
+    uniform points and, for short runs, a few exact ties across the two families."""
+    rng = np.random.default_rng(seed)
+    bins = rng.choice(1 << 31, n_bins, replace=False).astype(np.float64)
+    z = ((bins[:, None] + rng.random((n_bins, per_bin))) / 2.0 ** 31).ravel()
+    z = np.concatenate([z, rng.random(n_free)])
+    rng.shuffle(z)
+    cut = len(z) // 2
+    x, y = z[:cut].copy(), np.concatenate([[0.0, 1.0], z[cut:]])
+    if per_bin < 30:  # (a tie must not make a bin of 32 one of 33)
+        x[:50] = y[2:52]  # coordinates shared by a target and a source
+    return x, y
+
+
+@pytest.mark.parametrize("n_bins,per_bin,n_free", [(60000, 2, 0), (20000, 5, 100000), (3000, 32, 5000)])
+def test_perm_runs_of_equal_prefixes(cuda, n_bins, per_bin, n_free):
+    """Runs of equal prefix keys, up to the longest that the fix-up sorts (32 points),
+    some across tile boundaries: bit-exact."""
+    x, y = _binned(n_bins, per_bin, n_bins + per_bin, n_free)
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+
+
+@pytest.mark.parametrize("case", ["run_of_33", "narrow_cluster", "far_outlier"])
+def test_perm_full_sort_fallback(cuda, case):
+    """Runs of equal prefixes too long for the fix-up: one bin of 33 distinct points, a
+    cluster of 5000 distinct points 1e-13 wide, or every point in one bin because of a
+    coordinate at 1e300.  The full 64-bit sort runs; bit-exact."""
+    rng = np.random.default_rng(17)
+    if case == "run_of_33":
+        x, y = _binned(1, 33, 3, 50000)
+    else:
+        x, y, _ = inputs.uniform(70000, 60000, seed=18)
+        if case == "narrow_cluster":
+            x[:5000] = 0.5 + 1e-13 * rng.random(5000)
+        else:
+            y[7] = 1e300
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+
+
+def test_perm_negative_and_subnormal_ranges(cuda):
+    """Items whose coordinates are all negative, or all subnormal: bit-exact."""
+    rng = np.random.default_rng(19)
+    x, y = -rng.random(30000) * 7.0, -rng.random(25000) * 7.0 - 1e-3
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))
+    x, y = rng.random(20000) * 1e-310, rng.random(20000) * 1e-310
+    assert np.array_equal(_perm(x, y, cuda), oracle.sort_merged(x, y))

@@ -351,6 +351,53 @@ int run_pipeline(const fgt1d_plan_s& p, const double* x, int64_t M, const double
     return cuda_status(e);
 }
 
+// The transform of the point set that the previous run_pipeline on this workspace
+// sorted, with the roles of its points exchanged: targets x[M] (its sources), sources
+// y[N] (its targets) with strengths alpha.  Its sorted order is kept -- on equal
+// coordinates the targets now come first -- and so is its multiplier table when both
+// runs use the same sweeps (table_ok: FP64 or double-float entries of the same tile
+// shape, prev_ev the previous run's channels).  In the derivative channel a coincident
+// source then sits in h- instead of h+; coinc receives, for each target, the total
+// strength of the sources at its coordinate (the caller's correction changes sign).
+int run_pipeline_swapped(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha,
+                         int64_t N, double* u, double* out2, int ev, double* coinc, int prev_ev, char* ws,
+                         const Layout& L, cudaStream_t st) {
+    // sweep counters and look-back descriptors; the sort's plan, the equal-coordinate flag
+    // and the status stay
+    cudaError_t e = cudaMemsetAsync(ws + L.header + 64, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.fdesc, 0, L.zero_end - L.fdesc, st);
+    Item* items = reinterpret_cast<Item*>(ws + L.items);
+    int64_t* total_tiles = reinterpret_cast<int64_t*>(ws + L.header + 80);
+    if (e == cudaSuccess) e = launch_item_single(M, N, p.delta, items, total_tiles, st);
+    SortArgs sa = sort_args(y, N, x, M, ws, L);  // the previous run's view: targets y, sources x
+    if (e == cudaSuccess) e = launch_swap_codes(sa, M + N, M, N, st);
+    if (e != cudaSuccess) return FGT1D_ECUDA;
+    SweepArgs w = sweep_args(alpha, N, u, out2, ws, L);
+    if (coinc && (ev & 2)) w.ties = reinterpret_cast<uint32_t*>(ws + L.header + 88);  // set by the previous run
+    const bool f32 = (p.flags & FGT1D_FP32) != 0, df = (p.flags & FGT1D_F32X2) != 0;
+    const bool df_sweeps = df && ev == 1, prev_df = df && prev_ev == 1;
+    const int shape = shape_index(p, prev_ev);
+    w.reuse = (!f32 && df_sweeps == prev_df) ? 1 : 0;
+    SweepConsts c = make_consts(p);
+    if (f32) e = launch_sweeps_f32(w, c, st, nullptr, ev, shape);
+    else if (df_sweeps) e = launch_sweeps_df(w, c, st, nullptr, shape);
+    else e = launch_sweeps_f64(w, c, st, nullptr, ev, shape);
+    if (e == cudaSuccess && coinc && w.ties) {
+        // sums over sorted positions (every point evaluated), then each target takes its
+        // run's total; the forward partial sums are free again
+        double* F = reinterpret_cast<double*>(ws + L.fwd);
+        e = cudaMemsetAsync(ws + L.fdesc, 0, L.bdesc - L.fdesc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.tile_ctr, 0, sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(coinc, 0, sizeof(double) * (size_t)M, st);
+        SweepArgs wc = w;
+        wc.self = 1;
+        wc.u = F;
+        if (e == cudaSuccess) e = launch_coincidence(wc, c, st);
+        if (e == cudaSuccess) e = launch_coinc_gather(w, F, M + N, coinc, st);
+    }
+    return cuda_status(e);
+}
+
 int run_transform(const fgt1d_plan_s& p, const double* x, int64_t M, const double* y, const double* alpha, int64_t N,
                   double* u, char* ws, const Layout& L, cudaStream_t st, cudaEvent_t const* evs = nullptr,
                   cudaEvent_t alpha_ready = nullptr) {
@@ -522,12 +569,22 @@ extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const
         if (launch_grad_assemble(grad_u, D, A, sumV, M, gx, st) != cudaSuccess) return FGT1D_ECUDA;
     }
     if (need_a || need_y) {
-        // targets y, sources x, strengths grad_u: values -> dL/dalpha, derivative -> dL/dy / alpha
+        // targets y, sources x, strengths grad_u: values -> dL/dalpha, derivative -> dL/dy / alpha.
+        // After the first transform the same points are sorted already (and its multipliers
+        // tabulated): their order is kept, with coincident sources after their targets, so
+        // the coincidence correction changes sign
         const int ev = (need_a ? 1 : 0) | (need_y ? 2 : 0);
-        r = run_pipeline(*plan, y, N, x, grad_u, M, ItemSource(), grad_alpha, need_y ? D : nullptr, ev,
-                         need_y ? A : nullptr, ws, L, st);
+        double sign = 1.0;
+        if (need_x) {
+            r = run_pipeline_swapped(*plan, y, N, x, grad_u, M, grad_alpha, need_y ? D : nullptr, ev,
+                                     need_y ? A : nullptr, 2, ws, L, st);
+            sign = -1.0;
+        } else {
+            r = run_pipeline(*plan, y, N, x, grad_u, M, ItemSource(), grad_alpha, need_y ? D : nullptr, ev,
+                             need_y ? A : nullptr, ws, L, st);
+        }
         if (r) return r;
-        if (need_y && launch_grad_assemble(alpha, D, A, sumV, N, gy, st) != cudaSuccess) return FGT1D_ECUDA;
+        if (need_y && launch_grad_assemble(alpha, D, A, sign * sumV, N, gy, st) != cudaSuccess) return FGT1D_ECUDA;
     }
     if (grad_delta) {
         if (launch_grad_delta(x, gx, M, y, gy, N, plan->delta, reinterpret_cast<double*>(ws + L.parts), kGradPartials,

@@ -134,6 +134,9 @@ struct SortArgs {
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t st);
 // copies the first P sorted merged codes (item 0) to perm
 cudaError_t launch_copy_perm(const SortArgs& a, int64_t P, uint32_t* perm, cudaStream_t st);
+// Exchanges the roles of a sorted single item's points in its codes: sources [0, n_src)
+// become targets n_tgt + j, targets n_src + i become sources i (the order is kept).
+cudaError_t launch_swap_codes(const SortArgs& a, int64_t P, int64_t n_src, int64_t n_tgt, cudaStream_t st);
 
 // ---- sweeps (steps a3-a7) ----
 struct TileDesc {           // one (tile, term) entry of the decoupled look-back
@@ -201,6 +204,11 @@ cudaError_t launch_geometry_tag(uint64_t* tag, uint64_t value, cudaStream_t st);
 // identical points (a.self) u[p] is, per sorted position p, the sum over the points of
 // p's run of equal coordinates up to p.
 cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStream_t st);
+// Targets before sources on equal coordinates (roles exchanged after the sort): when the
+// equal-coordinate flag is set, A[i] = F[last position of target i's run of equal
+// coordinates], F from launch_coincidence with a.self set (sums over sorted positions),
+// i.e. the run's total source strength.
+cudaError_t launch_coinc_gather(const SweepArgs& a, const double* F, int64_t n, double* A, cudaStream_t st);
 // Identical points: u[point at sorted position p] += cf * F[last position of p's run of
 // equal coordinates], F from launch_coincidence (the run's total strength).
 cudaError_t launch_self_exact(const SweepArgs& a, const double* F, int64_t n, double cf, double* u, cudaStream_t st);

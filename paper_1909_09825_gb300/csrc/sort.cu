@@ -515,6 +515,7 @@ struct SortSmem {
     int item;
 };
 
+
 // PREFIX: a pass of the prefix sort: 32-bit prefix keys, with the codes and the full
 // 64-bit keys as payload (buffers: 0 = (pre, keysA, valsA), 1 = (pre + Ppad, keysB,
 // valsB)).  Otherwise a pass of the full sort (64-bit keys and codes, buffers A and B),
@@ -1001,6 +1002,7 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
         e = cudaFuncSetAttribute(k_sort_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sort_pass<false>, kSortThreads, smem64);
+
     if (e != cudaSuccess) return e;
     const int64_t tiles = a.max_tiles;
     const int hist_blocks = (int)std::min<int64_t>(tiles, (int64_t)sms * 4);
@@ -1013,7 +1015,7 @@ cudaError_t launch_sort(const SortArgs& a, cudaStream_t st) {
     for (int d = 0; d < kPrefixDigits; ++d) k_sort_pass<true><<<(unsigned)tiles, kSortThreads, smem32, st>>>(a, d);
     k_sort_merge<<<(unsigned)tiles, kSortThreads, sizeof(MergeSmem), st>>>(a);
     k_sort_detect<<<(unsigned)std::min<int64_t>(tiles, (int64_t)sms * 8), 256, 0, st>>>(a);
-    k_sort_fixup<<<sms * 4, 256, 0, st>>>(a);
+    k_sort_fixup<<<sms * 16, 256, 0, st>>>(a);
     // full sort after a fallback: grids of resident size, so that their blocks exit at
     // once when there is none
     k_sort_fb_prepare<<<sms * 4, 256, 0, st>>>(a);
@@ -1030,6 +1032,26 @@ __global__ void k_copy_perm(const uint32_t* __restrict__ va, const uint32_t* __r
     const uint32_t* v = plan->final_buf == 1 ? vb : va;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
         perm[i] = v[i];
+}
+
+// The sorted codes of a single item with the roles of its points exchanged: old
+// sources [0, n_src) become targets, old targets [n_src, n_src + n_tgt) sources (padding
+// codes stay).  The order is kept, so on equal coordinates the new targets come first.
+__global__ void k_swap_codes(uint32_t* __restrict__ va, uint32_t* __restrict__ vb, const SortPlan* plan, int64_t P,
+                             int64_t n_src, int64_t n_tgt) {
+    uint32_t* v = plan->final_buf == 1 ? vb : va;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = v[i];
+        if (q < n_src) v[i] = (uint32_t)(q + n_tgt);
+        else if (q < n_src + n_tgt) v[i] = (uint32_t)(q - n_src);
+    }
+}
+
+cudaError_t launch_swap_codes(const SortArgs& a, int64_t P, int64_t n_src, int64_t n_tgt, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((P + 255) / 256, 152 * 16);
+    k_swap_codes<<<blocks, 256, 0, st>>>(a.valsA, a.valsB, a.plan, P, n_src, n_tgt);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_perm(const SortArgs& a, int64_t P, uint32_t* perm, cudaStream_t st) {

@@ -38,35 +38,56 @@ cudaError_t launch_coincidence(const SweepArgs& a, const SweepConsts& c, cudaStr
     return cudaGetLastError();
 }
 
-// One thread per sorted position p of a single item of n identical points: the last
-// position of p's run of equal keys comes from a galloping search (steps 1, 2, 4, ...
-// while the key stays equal, then bisection of the last step), at most ~2 log2(n) key
-// loads for a run of any length and one for a point without ties.
+// The last position of sorted position p's run of equal keys (of n): a galloping search
+// (steps 1, 2, 4, ... while the key stays equal, then bisection of the last step), at
+// most ~2 log2(n) key loads for a run of any length and one for a point without ties.
+__device__ __forceinline__ int64_t run_last(const uint64_t* __restrict__ keys, int64_t p, int64_t n) {
+    const uint64_t k = keys[p];
+    if (p + 1 >= n || keys[p + 1] != k) return p;
+    int64_t lo = p + 1, step = 1;  // keys[lo] == k
+    while (lo + step < n && keys[lo + step] == k) {
+        lo += step;
+        step <<= 1;
+    }
+    int64_t hi = min(lo + step, n);  // keys[hi] != k, or hi == n
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (keys[mid] == k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One thread per sorted position p of a single item of n identical points.
 __global__ void __launch_bounds__(256) k_self_exact(const SweepArgs a, const double* __restrict__ F, int64_t n,
                                                     double cf, double* __restrict__ u) {
     const bool bufB = a.plan->final_buf == 1;
     const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
     const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
     if (*(volatile const uint32_t*)a.status & kStatusSortTimeout) return;  // sorted codes not valid
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        u[vals[p]] += cf * F[run_last(keys, p, n)];
+}
+
+// One thread per sorted position p of a single item of n points; targets only.
+__global__ void __launch_bounds__(256) k_coinc_gather(const SweepArgs a, const double* __restrict__ F, int64_t n,
+                                                      double* __restrict__ A) {
+    if (*(volatile const uint32_t*)a.status & kStatusSortTimeout) return;  // sorted codes not valid
+    if (!*(volatile const uint32_t*)a.ties) return;  // no coincident points: A stays zero
+    const bool bufB = a.plan->final_buf == 1;
+    const uint64_t* __restrict__ keys = bufB ? a.keysB : a.keysA;
+    const uint32_t* __restrict__ vals = bufB ? a.valsB : a.valsA;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = keys[p];
-        int64_t last = p;
-        if (p + 1 < n && keys[p + 1] == k) {
-            int64_t lo = p + 1, step = 1;  // keys[lo] == k
-            while (lo + step < n && keys[lo + step] == k) {
-                lo += step;
-                step <<= 1;
-            }
-            int64_t hi = min(lo + step, n);  // keys[hi] != k, or hi == n
-            while (hi - lo > 1) {
-                const int64_t mid = lo + (hi - lo) / 2;
-                if (keys[mid] == k) lo = mid;
-                else hi = mid;
-            }
-            last = lo;
-        }
-        u[vals[p]] += cf * F[last];
+        const int64_t v = vals[p];
+        if (v >= a.N && v < n) A[v - a.N] = F[run_last(keys, p, n)];  // (codes of points are below n)
     }
+}
+
+cudaError_t launch_coinc_gather(const SweepArgs& a, const double* F, int64_t n, double* A, cudaStream_t st) {
+    if (n <= 0 || !a.ties) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_coinc_gather<<<blocks, 256, 0, st>>>(a, F, n, A);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_self_exact(const SweepArgs& a, const double* F, int64_t n, double cf, double* u, cudaStream_t st) {

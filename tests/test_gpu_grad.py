@@ -129,3 +129,33 @@ def test_backward_edge_cases(cuda):
     rx, ry, ra, rd = oracle.grad_soe(xs, ys, al, 1e-3, plan.tau, plan.W, gg)
     assert np.allclose(gx, rx, rtol=1e-10, atol=1e-12) and np.allclose(gy, ry, rtol=1e-10, atol=1e-12)
     assert np.allclose(ga, ra, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f32x2"])
+@pytest.mark.parametrize("want", [(True, True, True, True), (True, True, False, False), (True, False, True, False),
+                                  (False, True, True, False), (False, False, True, True)])
+def test_backward_coincident_points(cuda, prec, want):
+    """Coordinates on a grid of 400 values: long runs of coincident targets and sources
+    (the second transform of the adjoint keeps the first one's sorted order, targets
+    before sources on a tie), every subset of the gradients, against the oracle's SOE
+    gradients (S'(0) = 0 for a coincident pair)."""
+    M, N, delta = 6000, 5000, 1e-3
+    x, y, a = inputs.uniform(M, N, seed=61)
+    x, y = np.round(x * 400) / 400, np.round(y * 400) / 400
+    g = np.random.default_rng(62).standard_normal(M)
+    n, tau, W, En = soe_cf.plan_soe(1e-6 if prec == "fp32" else 1e-8)
+    plan = fgt.Plan(delta, soe=(tau, W), precision=prec)
+    out = [t.cpu().numpy() if t is not None else None
+           for t in fgt.backward(plan, _dev(x, cuda), _dev(y, cuda), _dev(a, cuda), _dev(g, cuda), want=want)]
+    ref = oracle.grad_soe(x, y, a, delta, tau, W, g)
+    kappa = np.abs(tau).max() / np.sqrt(delta)
+    tol = 2e-5 if prec == "fp32" else 1e-11
+    scales = [tol * kappa * np.abs(g).max() * np.abs(a).sum(), tol * kappa * np.abs(a).max() * np.abs(g).sum(),
+              tol * np.abs(g).sum(), None]
+    for w, o, r, sc in zip(want, out, ref, scales):
+        assert (o is None) == (not w)
+        if w and sc is not None:
+            assert np.max(np.abs(o - r)) <= sc
+    if want[3]:
+        mag = (np.abs(x - x[0]) @ np.abs(ref[0]) + np.abs(y - x[0]) @ np.abs(ref[1])) / (2 * delta)
+        assert abs(out[3][0] - ref[3]) <= tol * (1 + kappa) * mag

@@ -41,7 +41,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # multiply-add of the recurrence (4) and the evaluation at targets (2 per target, half
 # of the points); plus 2 per point (difference and scaling of the gap).
 C_CE = 8
-KERNELS_PER_TRANSFORM = 15   # item table, histogram, pass plan, pass chain, 8 radix passes, merge, two sweeps
+# item table; sort: range, prefix maps, histogram, pass plan, pass chain, 4 prefix digit
+# passes, merge, run detection, fix-up, and the fallback's 13 kernels (launched, they
+# exit at once unless a run of equal prefixes is too long); two sweeps
+KERNELS_PER_TRANSFORM = 27
 WORKLOAD = ("plain FP64 at scale: M=N=2^26, x,y ~ U[0,1), alpha ~ N(0,1), delta=%g, eps=%g, unsorted "
             "inputs (sort timed), seed 0")
 
@@ -309,6 +312,13 @@ def main():
                       "algorithmic_ops_per_unit": "4 + 2 M/P FP64 ops per (merged point, term)"},
         "whole_transform": {"achieved": whole_ach, "frac": whole_ach / fp64_peak, "unit": "TFLOP/s",
                             "algorithmic_ops_per_unit": "n_e (C_ce + 20) FP64 ops per merged point"}}
+    # the sort moves memory: its algorithmic bytes against the measured copy bandwidth
+    hbm, hbm_src = hbm_peak()
+    passes = active_sort_passes(x, y)
+    sort_gbs = P * sort_bytes_per_point(passes) / (stages["sort_ms"] * 1e-3) / 1e9
+    roofline_more["sort"] = {"bound": "hbm", "achieved": sort_gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": sort_gbs / hbm, "peak_source": hbm_src, "digit_passes": passes,
+                             "algorithmic_bytes_per_point": sort_bytes_per_point(passes)}
     traffic = _traffic_record(plan)
     if traffic is not None:
         roofline["traffic"] = traffic * P
@@ -394,36 +404,59 @@ def hbm_peak():
     return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
+def _fixq(b, eh):
+    """sign(z) floor(|z| / 2^(eh - 1075)) from the bits b (uint64 array) of z."""
+    ef = ((b >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
+    m = b & np.uint64((1 << 52) - 1)
+    m = np.where(ef > 0, m | np.uint64(1 << 52), m)
+    sh = eh - np.maximum(ef, 1)
+    q = np.where(sh >= 64, np.uint64(0), m >> np.minimum(np.maximum(sh, 0), 63).astype(np.uint64)).astype(np.int64)
+    return np.where((b >> np.uint64(63)) == 1, -q, q)
+
+
 def active_sort_passes(x, y):
-    """Digit passes the sort runs on these points: the 8-bit digits of the
-    order-preserving keys that are not the same for every point."""
-    b = np.concatenate([y, x]).view(np.uint64).copy()
+    """Digit passes the sort runs on these points (one item): the 8-bit digits of the
+    32-bit prefix keys that are not the same for every point, padding included."""
+    z = np.concatenate([y, x])
+    b = z.view(np.uint64).copy()
     b[b == np.uint64(0x8000000000000000)] = 0  # -0.0 as +0.0
-    neg = (b >> np.uint64(63)) == 1
-    k = np.where(neg, ~b, b | np.uint64(0x8000000000000000))
+    lo, hi = b[np.argmin(z)], b[np.argmax(z)]
+    eh = max(1, int((lo >> np.uint64(52)) & np.uint64(0x7FF)), int((hi >> np.uint64(52)) & np.uint64(0x7FF)))
+    qlo, qhi = (int(_fixq(np.array([v], dtype=np.uint64), eh)[0]) for v in (lo, hi))
+    sh = max(0, (qhi - qlo).bit_length() - 32)
+    k = ((_fixq(b, eh) - qlo) >> sh).astype(np.uint64)
+    if len(z) % 4096:
+        k = np.append(k, np.uint64(0xFFFFFFFF))
     n = 0
-    for d in range(8):
+    for d in range(4):
         dg = (k >> np.uint64(8 * d)) & np.uint64(255)
         n += int(np.any(dg != dg[0]))
     return max(n, 1)
 
 
+def sort_bytes_per_point(passes):
+    """Algorithmic bytes per merged point of the prefix sort: the range pass reads the
+    coordinate (8), the histogram pass reads it again and writes the prefix key, full key
+    and code (8 + 16), each digit pass reads and writes those 16 bytes, and the run
+    detection reads the prefix and full keys (12)."""
+    return 8 + 24 + 32 * passes + 12
+
+
 def hbm_roofline_fp32(st, x, y, M, N):
     """HBM roofline of the FP32 path's two stages, which move memory rather than compute:
-    the sort (8 B read per point by the key/histogram pass, 24 B per point per digit pass:
-    key and code read and written) and the two sweeps (forward: key 8, code 4, strength
+    the sort (sort_bytes_per_point) and the two sweeps (forward: key 8, code 4, strength
     8 N/P, partial sum 4; backward: key 8, code 4, strength 8 N/P, partial sum 4, value
     8 M/P, code 4 M/P at targets)."""
     peak, src = hbm_peak()
     P = M + N
     passes = active_sort_passes(x, y)
-    sort_b = P * (8 + 24 * passes)
+    sort_b = P * sort_bytes_per_point(passes)
     sweep_b = P * (8 + 4 + 8 * N / P + 4) + P * (8 + 4 + 8 * N / P + 4 + 12 * M / P)
     sort_gbs = sort_b / (st["sort_ms"] * 1e-3) / 1e9
     sweep_gbs = sweep_b / ((st["fwd_sweep_ms"] + st["bwd_sweep_ms"]) * 1e-3) / 1e9
     return {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
             "sort": {"achieved": sort_gbs, "frac": sort_gbs / peak, "passes": passes,
-                     "algorithmic_bytes_per_point": 8 + 24 * passes},
+                     "algorithmic_bytes_per_point": sort_bytes_per_point(passes)},
             "sweeps": {"achieved": sweep_gbs, "frac": sweep_gbs / peak,
                        "algorithmic_bytes_per_point": sweep_b / P}}
 

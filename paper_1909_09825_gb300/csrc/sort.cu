@@ -729,29 +729,22 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a, int d
 
 
 // ---- the full keys, and runs of equal prefix keys ------------------------------------------
-// Lists run [s, s + len) for the fix-up.
-__device__ __forceinline__ void push_run(const SortArgs& a, uint64_t* runs, int64_t s, int len) {
-    const uint32_t idx = atomicAdd(&a.pplan->nruns, 1u);
-    if ((int64_t)idx < a.Ppad / 2) runs[idx] = (uint64_t)s | ((uint64_t)len << 40);
-    else atomicOr(&a.pplan->fallback, 1u);
-}
-
-// A run that starts at s inside a thread's window and reaches past it, its first len
-// points seen up to pos (exclusive; last key kprev, descent flag d): walks on while the
-// run lasts and lists it if it holds a descent.  A run longer than kRunMax is not
-// listed: the length check of its descents (check_extent) sends the sort to the fallback.
-__device__ __noinline__ void walk_run(const SortArgs& a, const uint32_t* pre, const uint64_t* keys, uint64_t* runs,
-                                      int64_t end, int64_t s, int64_t pos, uint32_t pk, uint64_t kprev, int len,
-                                      bool d) {
+// A run that starts inside a thread's window and reaches past it, its first len points
+// seen up to pos (exclusive; last key kprev, descent flag d): walks on while the run
+// lasts and returns its length when it is to be listed (it holds a descent), else 0.  A
+// run longer than kRunMax is not listed: the length check of its descents
+// (check_extent) sends the sort to the fallback.
+__device__ __noinline__ int walk_run(const uint32_t* pre, const uint64_t* keys, int64_t end, int64_t pos, uint32_t pk,
+                                     uint64_t kprev, int len, bool d) {
     while (pos < end && pre[pos] == pk) {
-        if (len >= kRunMax) return;
+        if (len >= kRunMax) return 0;
         const uint64_t kk = keys[pos];
         d |= kprev > kk;
         kprev = kk;
         ++len;
         ++pos;
     }
-    if (d) push_run(a, runs, s, len);
+    return d ? len : 0;
 }
 
 // A descent in a run of prefix pk that holds points [lo, hi) and may extend below lo
@@ -786,6 +779,8 @@ __global__ void __launch_bounds__(256) k_sort_detect(SortArgs a) {
         const int64_t g0 = t * kTile + threadIdx.x * kSortIPT;  // a multiple of 16
         uint32_t p[kSortIPT];
         uint64_t k[kSortIPT];
+        uint32_t lst = 0, eqm = 0;
+        int xlen = 0, xq = 0;
 #pragma unroll
         for (int q = 0; q < kSortIPT / 4; ++q) {
             const uint4 pp = reinterpret_cast<const uint4*>(pre + g0)[q];
@@ -798,7 +793,7 @@ __global__ void __launch_bounds__(256) k_sort_detect(SortArgs a) {
         }
         if (g0 + 1 < end) {
             const uint32_t p16 = g0 + kSortIPT < end ? pre[g0 + kSortIPT] : ~p[kSortIPT - 1];
-            uint32_t eqm = 0, dsm = 0;
+            uint32_t dsm = 0;
 #pragma unroll
             for (int q = 0; q < kSortIPT; ++q) {
                 const uint32_t pn = q + 1 < kSortIPT ? p[q + 1] : p16;
@@ -813,15 +808,20 @@ __global__ void __launch_bounds__(256) k_sort_detect(SortArgs a) {
                     if (k[kSortIPT - 1] > k16) dsm |= 1u << 15;
                 }
                 const bool before = g0 > start && pre[g0 - 1] == p[0];  // the first run began earlier
-                // runs that start in the window
+                // runs that start in the window: bit q of lst for a run inside it with a
+                // descent; the run that reaches past the window is followed by walk_run
                 uint32_t st = eqm & ~((eqm << 1) | (before ? 1u : 0u));
                 while (st) {
                     const int q = __ffs(st) - 1;
                     st &= st - 1;
                     const int j = __ffs(~(eqm >> q)) - 1;  // equal pairs from q: points q .. q + j
                     const bool d = (dsm & (((1u << j) - 1u) << q)) != 0;
-                    if (q + j == kSortIPT) walk_run(a, pre, keys, runs, end, g0 + q, g0 + kSortIPT + 1, p[q], k16, j + 1, d);
-                    else if (d) push_run(a, runs, g0 + q, j + 1);
+                    if (q + j == kSortIPT) {
+                        xlen = walk_run(pre, keys, end, g0 + kSortIPT + 1, p[q], k16, j + 1, d);
+                        xq = q;
+                    } else if (d) {
+                        lst |= 1u << q;
+                    }
                 }
                 // descents in runs that reach outside the window
                 const int j0 = __ffs(~eqm) - 1;  // equal pairs from point 0
@@ -835,41 +835,66 @@ __global__ void __launch_bounds__(256) k_sort_detect(SortArgs a) {
                 }
             }
         }
+        // the listed runs go out with one counter update per warp
+        const uint32_t cnt = __popc(lst) + (xlen > 0 ? 1u : 0u);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t2 = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((threadIdx.x & 31) >= o) inc += t2;
+        }
+        uint32_t wbase = 0;
+        if ((threadIdx.x & 31) == 31 && inc) wbase = atomicAdd(&a.pplan->nruns, inc);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        if (cnt) {
+            int64_t idx = (int64_t)wbase + inc - cnt;
+            if (idx + cnt > a.Ppad / 2) {
+                atomicOr(&a.pplan->fallback, 1u);
+            } else {
+                while (lst) {
+                    const int q = __ffs(lst) - 1;
+                    lst &= lst - 1;
+                    const int len = __ffs(~(eqm >> q));  // points q .. q + j
+                    runs[idx++] = (uint64_t)(g0 + q) | ((uint64_t)len << 40);
+                }
+                if (xlen > 0) runs[idx] = (uint64_t)(g0 + xq) | ((uint64_t)xlen << 40);
+            }
+        }
         __syncthreads();  // s_item is rewritten for the next tile
     }
 }
 
-// One warp per listed run: each lane takes one point, ranks it by (key, code) among the
-// run's points, and writes it back in place (the final buffer of the prefix sort).
+// One thread per listed run (at most kRunMax points, nearly always two or three): an
+// insertion sort by (key, code) in local arrays, written back in place (the final
+// buffer of the prefix sort).
 __global__ void __launch_bounds__(256) k_sort_fixup(SortArgs a) {
     if (a.plan->merge || a.pplan->fallback || (*a.status & kStatusSortTimeout)) return;
     const int fb = a.pplan->final_buf;
     uint64_t* keys = fb ? a.keysB : a.keysA;
     uint32_t* vals = fb ? a.valsB : a.valsA;
     const uint64_t* runs = reinterpret_cast<const uint64_t*>(a.pre + (fb ? 0 : a.Ppad));
-    const uint32_t n = (uint32_t)min((int64_t)a.pplan->nruns, a.Ppad / 2);
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
+    const int64_t n = min((int64_t)a.pplan->nruns, a.Ppad / 2);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = runs[r];
         const int64_t s = (int64_t)(e & ((1ull << 40) - 1));
-        const int len = (int)(e >> 40);
-        uint64_t k = ~0ull;
-        uint32_t v = 0xFFFFFFFFu;
-        if (lane < len) {
-            k = keys[s + lane];
-            v = vals[s + lane];
+        const int len = min((int)(e >> 40), kRunMax);
+        uint64_t k[kRunMax];
+        uint32_t v[kRunMax];
+        for (int i = 0; i < len; ++i) {
+            const uint64_t ki = keys[s + i];
+            const uint32_t vi = vals[s + i];
+            int j = i;
+            while (j > 0 && (k[j - 1] > ki || (k[j - 1] == ki && v[j - 1] > vi))) {
+                k[j] = k[j - 1];
+                v[j] = v[j - 1];
+                --j;
+            }
+            k[j] = ki;
+            v[j] = vi;
         }
-        int rank = 0;
-        for (int j = 0; j < len; ++j) {
-            const uint64_t kj = __shfl_sync(0xffffffffu, k, j);
-            const uint32_t vj = __shfl_sync(0xffffffffu, v, j);
-            rank += (kj < k || (kj == k && vj < v)) ? 1 : 0;
-        }
-        __syncwarp();
-        if (lane < len) {
-            keys[s + rank] = k;
-            vals[s + rank] = v;
+        for (int i = 0; i < len; ++i) {
+            keys[s + i] = k[i];
+            vals[s + i] = v[i];
         }
     }
 }

@@ -38,7 +38,8 @@
  *    Two environment variables, read at every call, exist to test this path without a
  *    GPU fault: FGT1D_SPIN_LIMIT_CYCLES (a positive integer of SM clock cycles)
  *    replaces the bound, and FGT1D_FAULT=sweep_timeout or sort_timeout makes one wait
- *    of the forward sweep or of each sort pass run out (tile 0 is never processed).
+ *    of the forward sweep or of each prefix sort pass run out (tile 0 is never
+ *    processed).
  *    After an expired sort wait the results are not written.  Leave both unset in use.
  */
 #ifndef FGT1D_H
@@ -309,8 +310,9 @@ int fgt1d_segment_apply(fgt1d_plan plan, int64_t M, int64_t N, const double* car
  * channel Re sum_k V_k (h+ - h-), V_k = -tau_k W_k / sqrt(delta); grad_delta uses the
  * scale invariance sum x dL/dx + sum y dL/dy + 2 delta dL/ddelta = 0.  Device arrays:
  * grad_u[M]; outputs grad_x[M], grad_y[N], grad_alpha[N], grad_delta[1], any of which
- * may be NULL (not computed).  Workspace from fgt1d_backward_workspace_size.
- * Stream-ordered like fgt1d_execute. */
+ * may be NULL (not computed).  When grad_x or grad_delta is requested, the second sum
+ * (targets y, sources x) reuses the first one's sorted points and multipliers.
+ * Workspace from fgt1d_backward_workspace_size.  Stream-ordered like fgt1d_execute. */
 int fgt1d_backward_workspace_size(fgt1d_plan plan, int64_t M, int64_t N, size_t* bytes);
 int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y, const double* alpha,
                    int64_t N, const double* grad_u, double* grad_x, double* grad_y, double* grad_alpha,
@@ -321,7 +323,11 @@ int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const double* y,
  * sorted position p.  Workspace from fgt1d_sort_workspace_size.  Like every entry point
  * that sorts, it detects sources and targets that each arrive in non-decreasing order
  * (Sec. 5's pre-sorted points) and then merges the two runs in one pass instead of
- * running the radix passes; the permutation is the same either way. */
+ * running the radix passes; the permutation is the same either way.  The radix passes
+ * sort 32-bit keys that are a non-decreasing function of the coordinate within its
+ * item's range and fix up the few runs of equal keys; when a run of more than 32
+ * distinct coordinates shares one key (a cluster narrower than the range / 2^32), the
+ * full 64-bit sort runs instead, with the same result. */
 int fgt1d_sort_workspace_size(int64_t M, int64_t N, size_t* bytes);
 int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,
                       void* workspace, size_t ws_bytes, fgt1d_stream stream);

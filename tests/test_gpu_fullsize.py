@@ -8,7 +8,9 @@ alpha ~ N(0, 1), seed 0, in the launch configuration bench.py times (default til
 * 1000 sampled targets against the direct Gauss sum over all 2^26 sources (eq. 1.1),
   within 2 eps + 1e-13 (FP64), and the oracle's own recurrence error at those targets;
 * the sorted merged order of all 2^27 points, bit for bit, against the oracle's stable
-  sort.
+  sort;
+* the clustered mixture workload at the same size: its sorted order bit for bit and
+  every target of the FP64 transform.
 
 Tolerances: FP64 within 1e-12 sum|alpha| of the oracle's recurrence (both are the same
 SOE operator; what differs is rounding order: chunked scans with directly computed span
@@ -91,4 +93,24 @@ def test_fullsize_permutation_bit_exact(data):
     assert perm.shape == ref.shape == (2 * M,)
     assert np.array_equal(perm, ref)
     del perm
+    torch.cuda.empty_cache()
+
+
+def test_fullsize_mixture_permutation_and_every_target(cuda):
+    """The clustered workload at full size (8 Gaussians of width 1e-3 plus 10 % uniform,
+    M = N = 2^26, the mixture configuration bench.py times): about one point per 32-bit
+    sort key inside the clusters, so millions of runs of equal keys go through the
+    fix-up.  The sorted order bit for bit against the oracle's stable sort, and every
+    target of the FP64 transform against the oracle's recurrence."""
+    x, y, a = inputs.mixture(M, N, seed=0)
+    X, Y, A = (torch.from_numpy(v).to(cuda) for v in (x, y, a))
+    perm = fgt.sort_merged(X, Y).cpu().numpy()
+    assert np.array_equal(perm, oracle.sort_merged_par(x, y))
+    del perm
+    delta, eps = 1e-4, 1e-6
+    _, tau, W, _ = soe_cf.plan_soe(eps)
+    u = fgt.transform(fgt.Plan(delta, soe=(tau, W)), X, Y, A).cpu().numpy()
+    ref = oracle.recurrence_par(x, y, a, delta, tau, W)
+    assert np.max(np.abs(u - ref)) / np.abs(a).sum() <= 1e-12
+    del X, Y, A, u
     torch.cuda.empty_cache()

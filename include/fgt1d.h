@@ -148,6 +148,18 @@ int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const d
                        const double* alpha_host, int64_t N, double* u_host, void* workspace,
                        size_t ws_bytes, fgt1d_stream stream);
 
+/* fgt1d_execute_host without the final synchronisation (no counterpart in the paper):
+ * the copies in, the transform and the copy of u out are enqueued on `stream` (the
+ * strengths' copy on a second stream that the transform waits for) and the call
+ * returns.  The host arrays must stay valid, and u_host unread, until the stream's work
+ * is done; fgt1d_check(workspace, ws_bytes, stream) then waits and returns the device
+ * status.  With pinned host arrays, calls on two streams with two workspaces overlap
+ * one transform's copies with the other's kernels.  Arguments and argument errors as
+ * fgt1d_execute_host (M = 0 and N = 0 are handled on the host at once). */
+int fgt1d_execute_host_async(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
+                             const double* alpha_host, int64_t N, double* u_host, void* workspace,
+                             size_t ws_bytes, fgt1d_stream stream);
+
 /* A batch of B independent transforms of uneven sizes and bandwidths in one pass of
  * the same kernels (the same method per item; the paper treats one transform).  Item b
  * has targets x[x_off[b] .. x_off[b+1]), sources y and strengths alpha at

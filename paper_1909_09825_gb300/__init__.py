@@ -7,6 +7,6 @@ and the sorted forward/backward recurrences of Sec. 4.  Every step runs in the
 CUDA library libfgt1d.so (C ABI in include/fgt1d.h); this package only marshals
 arguments.  Import is lazy: the library is loaded on first use.
 """
-from .fgt1d import (Plan, soe_cf, transform, sort_merged, execute_host, Workspace, backward,  # noqa: F401
+from .fgt1d import (Plan, soe_cf, transform, sort_merged, execute_host, wait_host, Workspace, backward,  # noqa: F401
                     GaussTransform, gauss_transform, transform_batched, Geometry,
                     transform_self)

@@ -40,6 +40,7 @@ SIGNATURES = {
     "fgt1d_execute_profiled": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P, _P]),
     "fgt1d_workspace_size_host": (_I, [_P, _I64, _I64, _P]),
     "fgt1d_execute_host": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "fgt1d_execute_host_async": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),
     "fgt1d_execute_noalloc": (_I, [_P, _P, _I64, _P, _P, _I64, _P, _P]),
     "fgt1d_batched_workspace_size": (_I, [_P, _I, _I64, _I64, _P]),
     "fgt1d_execute_batched": (_I, [_P, _I, _P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _SZ, _P]),

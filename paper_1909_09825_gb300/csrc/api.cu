@@ -594,9 +594,13 @@ extern "C" int fgt1d_backward(fgt1d_plan plan, const double* x, int64_t M, const
     return FGT1D_OK;
 }
 
-extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
-                                  const double* alpha_host, int64_t N, double* u_host, void* workspace,
-                                  size_t ws_bytes, fgt1d_stream stream) {
+namespace fgt1d {
+namespace {
+
+// fgt1d_execute_host and its asynchronous form: copies in, the transform, the copy out;
+// with sync the stream is synchronised and the device status returned.
+int execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host, const double* alpha_host,
+                 int64_t N, double* u_host, void* workspace, size_t ws_bytes, fgt1d_stream stream, bool sync) {
     if (!plan || !sizes_ok(M, N)) return FGT1D_EINVAL;
     if (M > 0 && (!x_host || !u_host)) return FGT1D_EINVAL;
     if (N > 0 && M > 0 && (!y_host || !alpha_host)) return FGT1D_EINVAL;
@@ -643,7 +647,22 @@ extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t
     release();  // the stream and events go once their work is done
     if (cudaMemcpyAsync(u_host, du, sizeof(double) * (size_t)M, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return FGT1D_ECUDA;
-    return fgt1d_check(workspace, ws_bytes, stream);
+    return sync ? fgt1d_check(workspace, ws_bytes, stream) : FGT1D_OK;
+}
+
+}  // namespace
+}  // namespace fgt1d
+
+extern "C" int fgt1d_execute_host(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
+                                  const double* alpha_host, int64_t N, double* u_host, void* workspace,
+                                  size_t ws_bytes, fgt1d_stream stream) {
+    return execute_host(plan, x_host, M, y_host, alpha_host, N, u_host, workspace, ws_bytes, stream, true);
+}
+
+extern "C" int fgt1d_execute_host_async(fgt1d_plan plan, const double* x_host, int64_t M, const double* y_host,
+                                        const double* alpha_host, int64_t N, double* u_host, void* workspace,
+                                        size_t ws_bytes, fgt1d_stream stream) {
+    return execute_host(plan, x_host, M, y_host, alpha_host, N, u_host, workspace, ws_bytes, stream, false);
 }
 
 extern "C" int fgt1d_sort_merged(const double* x, int64_t M, const double* y, int64_t N, uint32_t* perm,

@@ -184,9 +184,11 @@ def transform(plan, x, y, alpha, out=None, workspace=None, stream=None, sync_che
     return out
 
 
-def execute_host(plan, x, y, alpha, out=None, workspace=None, stream=None):
+def execute_host(plan, x, y, alpha, out=None, workspace=None, stream=None, sync=True):
     """End-to-end transform of HOST numpy arrays through fgt1d_execute_host (copies in,
-    transform, copy out, synchronise)."""
+    transform, copy out, synchronise).  With sync=False, fgt1d_execute_host_async: the
+    work is only enqueued on `stream`; `out` is valid, and the arrays may be reused, after
+    wait_host(workspace, stream) (or a synchronisation of the stream)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     alpha = np.ascontiguousarray(alpha, dtype=np.float64)
@@ -195,9 +197,16 @@ def execute_host(plan, x, y, alpha, out=None, workspace=None, stream=None):
         out = np.empty(M, dtype=np.float64)
     nbytes = plan.workspace_size(M, N, host=True)
     ws = _workspace(workspace, torch.device("cuda", torch.cuda.current_device()), nbytes)
-    check(lib().fgt1d_execute_host(plan.handle, _ptr(x), M, _ptr(y), _ptr(alpha), N, _ptr(out),
-                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)), "execute_host")
+    f = lib().fgt1d_execute_host if sync else lib().fgt1d_execute_host_async
+    check(f(plan.handle, _ptr(x), M, _ptr(y), _ptr(alpha), N, _ptr(out), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+            _stream_ptr(stream)), "execute_host")
     return out
+
+
+def wait_host(workspace, stream=None):
+    """Waits for an execute_host(..., sync=False) on `stream` and raises on a device error."""
+    ws = workspace.get(0) if isinstance(workspace, Workspace) else workspace
+    check(lib().fgt1d_check(ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)), "execute_host (device)")
 
 
 def sort_merged(x, y, workspace=None, stream=None):

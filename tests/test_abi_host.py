@@ -255,3 +255,23 @@ def test_autotune_takes_a_cached_choice_without_timing(L, tmp_path, monkeypatch)
                           ctypes.byref(chosen), ms)
     assert rc == _lib.FGT1D_OK and chosen.value == 128 and p.tile_threads == 128
     assert list(ms) == [-1.0, -1.0]
+
+
+def test_execute_host_async_argument_errors(L):
+    """The asynchronous host-buffer entry point checks its arguments on the host, as the
+    synchronous one does, before any CUDA call; M = 0 is a no-op and N = 0 writes u = 0
+    at once (host memory, no GPU needed)."""
+    import paper_1909_09825_gb300 as fgt
+    from paper_1909_09825_gb300 import _lib
+    p = fgt.Plan(1e-3, 1e-6)
+    v = (ctypes.c_double * 8)(*range(8))
+    f = L.fgt1d_execute_host_async
+    assert f(p.handle, None, 8, v, v, 8, v, None, 0, None) == _lib.FGT1D_EINVAL     # x
+    assert f(p.handle, v, 8, None, v, 8, v, None, 0, None) == _lib.FGT1D_EINVAL     # y
+    assert f(p.handle, v, 8, v, None, 8, v, None, 0, None) == _lib.FGT1D_EINVAL     # alpha
+    assert f(p.handle, v, 8, v, v, 8, None, None, 0, None) == _lib.FGT1D_EINVAL     # u
+    assert f(None, v, 8, v, v, 8, v, None, 0, None) == _lib.FGT1D_EINVAL            # plan
+    assert f(p.handle, v, -1, v, v, 8, v, None, 0, None) == _lib.FGT1D_EINVAL       # size
+    assert f(p.handle, None, 0, v, v, 8, None, None, 0, None) == _lib.FGT1D_OK      # M = 0
+    assert f(p.handle, v, 8, None, None, 0, v, None, 0, None) == _lib.FGT1D_OK      # N = 0
+    assert list(v) == [0.0] * 8

@@ -313,6 +313,28 @@ def test_execute_host_matches_device(cuda):
     assert np.array_equal(u_dev, u_host)
 
 
+def test_execute_host_async_two_streams(cuda):
+    """Two fgt1d_execute_host_async calls in flight on two streams with two workspaces
+    (pinned host arrays), then a third on the first stream after its wait: each result
+    agrees with the device-buffer transform of its inputs to rounding (the look-back's
+    order of predecessors depends on timing, as in test_repeat_runs_agree)."""
+    plan = fgt.Plan(1e-3, 1e-6)
+    runs = [inputs.uniform(70000, 60000, seed=s) for s in (11, 12)]
+    pinned = [[torch.from_numpy(v).pin_memory().numpy() for v in r] for r in runs]
+    outs = [torch.empty(70000, dtype=torch.float64).pin_memory().numpy() for _ in runs]
+    streams = [torch.cuda.Stream(cuda) for _ in runs]
+    wss = [fgt.Workspace(cuda) for _ in runs]
+    for (x, y, a), o, st, ws in zip(pinned, outs, streams, wss):
+        fgt.execute_host(plan, x, y, a, out=o, workspace=ws, stream=st, sync=False)
+    for o, st, ws, (x, y, a) in zip(outs, streams, wss, runs):
+        fgt.wait_host(ws, st)
+        assert rel_inf(o, gpu_transform(plan, x, y, a), a) <= TOL_ARITH64
+    x, y, a = pinned[1]
+    fgt.execute_host(plan, x, y, a, out=outs[0], workspace=wss[0], stream=streams[0], sync=False)
+    fgt.wait_host(wss[0], streams[0])
+    assert rel_inf(outs[0], gpu_transform(plan, *runs[1]), runs[1][2]) <= TOL_ARITH64
+
+
 def test_repeat_runs_agree(cuda):
     """The decoupled look-back adds a timing-dependent set of predecessor aggregates,
     so repeated runs may differ in rounding only (never by more than TOL_ARITH64)."""

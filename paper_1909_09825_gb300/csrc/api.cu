@@ -22,7 +22,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // upper bounds for B items totalling M targets and N sources: each item pads its merged
 // range to whole tiles, which adds at most one tile per item.
 struct Layout {
-    size_t header = 0;       // status (u32 at 0), sort tile counters (8 u32 at 32), sweep tile
+    size_t header = 0;       // status (u32 at 0), full-sort tile counters (8 u32 at 32), sweep tile
                              // counters (2 u32 at 64), total tiles (i64 at 80), equal-coordinate
                              // flag (u32 at 88), geometry tag (u64 at 96), SortPlan at 128
     size_t hist = 0, offs = 0, sort_desc = 0, fdesc = 0, bdesc = 0;

@@ -59,7 +59,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 16;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 static_assert(kSortTile == kTile, "sort tiles and item padding share one size");
-// Longest run of equal prefix keys that the fix-up sorts (one warp per run); a longer
+// Longest run of equal prefix keys that the fix-up sorts (one thread per run); a longer
 // run with coordinates out of order sends the sort to the full 64-bit passes.
 constexpr int kRunMax = 32;
 // Default upper bound on one inter-block spin wait, in SM clock cycles (about 2 s at

@@ -26,7 +26,7 @@
 //           full keys through the same shared words);
 //   detect  the neighbour pairs with equal prefixes whose keys are out of order list
 //           their runs (first position and length);
-//   fix-up  one warp sorts each listed run by (key, merged index).
+//   fix-up  one thread sorts each listed run by (key, merged index).
 // Carrying the full keys costs 12 bytes per point and pass; reading them back by code
 // after the passes would cost a random 8-byte read per point, about 64 bytes of DRAM
 // traffic each on this part.  A run longer than kRunMax with keys out of order (a

@@ -183,3 +183,35 @@ def test_batched_presorted_items(cuda):
             continue
         ref = oracle.recurrence(xs, ys, al, d[i], tau, W)
         assert np.max(np.abs(u[x_off[i]:x_off[i + 1]] - ref)) / np.abs(al).sum() <= TOL_ARITH64, i
+
+
+@pytest.mark.parametrize("case", ["ranges", "fallback"])
+def test_batched_items_with_their_own_sort_keys(cuda, case):
+    """Every item sorts on 32-bit keys over its own coordinate range: items on shifted,
+    scaled and negative ranges, one of subnormal coordinates, one holding ties across its
+    sources and targets, and (case "fallback") one with 3000 distinct targets inside
+    1e-13, which makes the whole batch take the full 64-bit sort.  Item by item against
+    the oracle's recurrence."""
+    rng = np.random.default_rng(31)
+    items = [(rng.random(2500), rng.random(2000)),
+             (5.0 + 1e-3 * rng.random(3000), 5.0 + 1e-3 * rng.random(2600)),
+             (-7.0 * rng.random(1200), -7.0 * rng.random(1500) - 1e-6),
+             (1e-310 * rng.random(800), 1e-310 * rng.random(900)),
+             (np.round(rng.random(4000) * 300) / 300, np.round(rng.random(3500) * 300) / 300)]
+    if case == "fallback":
+        items.append((0.5 + 1e-13 * rng.random(3000), rng.random(2000)))
+    sx = [len(p[0]) for p in items]
+    sy = [len(p[1]) for p in items]
+    x_off = np.concatenate([[0], np.cumsum(sx)]).astype(np.int64)
+    y_off = np.concatenate([[0], np.cumsum(sy)]).astype(np.int64)
+    x = np.concatenate([p[0] for p in items])
+    y = np.concatenate([p[1] for p in items])
+    a = rng.standard_normal(len(y))
+    d = 10.0 ** rng.uniform(-6, -2, len(items))
+    n, tau, W, En = soe_cf.plan_soe(1e-8)
+    plan = fgt.Plan(1.0, soe=(tau, W))
+    u = _run(plan, (x_off, y_off, d, x, y, a), cuda)
+    for i in range(len(items)):
+        xs, ys, al = x[x_off[i]:x_off[i + 1]], y[y_off[i]:y_off[i + 1]], a[y_off[i]:y_off[i + 1]]
+        ref = oracle.recurrence(xs, ys, al, d[i], tau, W)
+        assert np.max(np.abs(u[x_off[i]:x_off[i + 1]] - ref)) / np.abs(al).sum() <= TOL_ARITH64, i

@@ -207,6 +207,8 @@ def main():
                     help="sweep tile threads; 0 = autotune each configuration (default)")
     ap.add_argument("--precision", default=HEAD["precision"], choices=["fp64", "fp32", "f32x2"],
                     help="precision of the headline configuration (profiling runs)")
+    ap.add_argument("--section", default=None, choices=["batched", "differentiation"],
+                    help="run only this extra section and print its record (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -223,6 +225,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.section:
+        rec = batched(dev, world, check=False) if args.section == "batched" else differentiation(dev, world)
+        if rank == 0:
+            print(json.dumps({"section": args.section, **rec}))
+        return
 
     def barrier():
         if world > 1:
